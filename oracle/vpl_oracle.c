@@ -1,0 +1,861 @@
+/*
+ * FP64 CPU oracle for the hybrid close-range VPL method
+ * (Jin, Wang, Zheng, Hua, Huo: "A Virtual Point Light Generation Method in
+ * Close-Range Area", arXiv 2203.11484).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the GPU path computes.  It shares no code with the CUDA
+ * library; only the test-suite, the smoke check and the benchmark's CPU
+ * baseline load it.  Everything is double precision, compiled with
+ * -ffp-contract=off so every product and sum is rounded on its own.
+ *
+ * Paper passages followed (Sec. 3 unless noted):
+ *   Eq. 1                 L(y) ~ Le(y) + sum_i G_i V_i L_i  (indirect part only)
+ *   close/distant split   one-sided face, inside the field of view, nearer
+ *                         than a threshold  -> close range
+ *   pipeline (1)-(4)      classify; patch sampling of the close range; instant
+ *                         radiosity over the whole scene keeping only hits on
+ *                         the distant part; render
+ *   Eq. 2                 patch VPL value L_i = G_i V_i L_e, G_i = D cos w/(4 pi r^2)
+ *   "Realization"         Morton order of the close triangles, area prefix sum
+ *                         f(i), inverse g, K equal-area strata, random points in
+ *                         the chosen triangle, each VPL carrying the area of its
+ *                         stratum
+ *
+ * Readings where the paper is silent or garbled (the same ones the GPU path
+ * implements, listed with reasons in the design notes):
+ *   - "camera" in the definition of w and r in Eq. 2 means the light;
+ *   - a patch VPL stores reflected power: albedo x incident power on its area;
+ *   - close-range test on the triangle centroid, front-facing to the camera,
+ *     and facing the light (no occlusion test);
+ *   - integer-quantised areas so that stratum -> triangle is exact;
+ *   - instant-radiosity paths start at the first bounce, no roulette, a hit on
+ *     a close face stores nothing but the path continues, the first m_far VPLs
+ *     in (path, bounce) order are kept and all are divided by the number of
+ *     paths P that were needed;
+ *   - random numbers: Philox4x64-10 (Salmon et al., SC'11) with counter
+ *     (index, sub-index, 0, 0) and key (seed, stream); u = (w >> 40) * 2^-24.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------ */
+/* small FP64 vector algebra (each op rounded separately)                   */
+/* ------------------------------------------------------------------------ */
+typedef struct { double x, y, z; } d3;
+
+static d3 mk(double x, double y, double z) { d3 r = {x, y, z}; return r; }
+static d3 add(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static d3 sub(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static d3 scl(d3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static double dot(d3 a, d3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+static d3 cross(d3 a, d3 b) {
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double len(d3 a) { return sqrt(dot(a, a)); }
+static d3 unit(d3 a) { double l = len(a); return mk(a.x / l, a.y / l, a.z / l); }
+static d3 ld3(const double *p) { return mk(p[0], p[1], p[2]); }
+static d3 lf3(const float *p) { return mk((double)p[0], (double)p[1], (double)p[2]); }
+static void st3(double *p, d3 a) { p[0] = a.x; p[1] = a.y; p[2] = a.z; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+
+static const double PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)                        */
+/* ------------------------------------------------------------------------ */
+ORC_API void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        unsigned __int128 p0 = (unsigned __int128)M0 * c0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * c2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+enum { STREAM_PATCH = 1, STREAM_LIGHT = 2, STREAM_IR = 3 };
+
+static void rng4(uint64_t seed, uint64_t stream, uint64_t i, uint64_t j, uint64_t w[4])
+{
+    uint64_t ctr[4] = {i, j, 0, 0}, key[2] = {seed, stream};
+    orc_philox4x64_10(ctr, key, w);
+}
+
+/* top 24 bits of a word as a number in [0, 1) (exact in FP32 and FP64) */
+static double u01(uint64_t w) { return (double)(w >> 40) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------------ */
+/* Morton code: bit i of qx, qy, qz goes to bit 3i+2, 3i+1, 3i                */
+/* ------------------------------------------------------------------------ */
+ORC_API uint64_t orc_morton63(uint32_t qx, uint32_t qy, uint32_t qz)
+{
+    uint64_t code = 0;
+    for (int i = 0; i < 21; i++) {
+        code |= (uint64_t)((qx >> i) & 1u) << (3 * i + 2);
+        code |= (uint64_t)((qy >> i) & 1u) << (3 * i + 1);
+        code |= (uint64_t)((qz >> i) & 1u) << (3 * i);
+    }
+    return code;
+}
+
+static uint32_t quant21(double v, double lo, double hi)
+{
+    double t = (hi > lo) ? (v - lo) / (hi - lo) : 0.0;
+    double q = floor(t * 2097152.0);
+    if (q > 2097151.0) q = 2097151.0;
+    if (q < 0.0) q = 0.0;
+    return (uint32_t)q;
+}
+
+/* ------------------------------------------------------------------------ */
+/* scene                                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    d3 lo, hi;
+    int32_t left, right;   /* children (internal) */
+    int32_t first, count;  /* triangle range in perm[] (leaf when count > 0) */
+} onode;
+
+typedef struct {
+    int64_t nt;
+    d3 *a, *e1, *e2, *cr, *n, *g;
+    double *area, *rho;
+    d3 glo, ghi;           /* AABB of all centroids   */
+    d3 vlo, vhi;           /* AABB of all vertices    */
+    onode *nodes;
+    int32_t n_nodes;
+    int32_t *perm;
+} oscene;
+
+typedef struct {
+    double eye[3], fwd[3], up[3];
+    double vfov_deg;
+    int32_t width, height;
+} ocamera;
+
+typedef struct {
+    double center[3], normal[3], edge_u[3], edge_v[3], power[3];
+    int32_t type;          /* 0 one-sided square area light, 1 isotropic point light */
+} olight;
+
+typedef struct {
+    double d_close;
+    double ray_eps;
+    int64_t ir_max_paths;
+    uint64_t seed;
+    int32_t m_close, m_far, max_bounces, light_samples;
+    int32_t vis_mode;      /* 0 BVH, 1 brute force */
+} ogen;
+
+/* ---- FP64 BVH: top-down median split, boxes padded so that the set of
+ *      candidate triangles is always a superset of the true hits ---------- */
+static const d3 *g_sort_g;
+static int g_sort_axis;
+static int cmp_axis(const void *pa, const void *pb)
+{
+    int32_t ia = *(const int32_t *)pa, ib = *(const int32_t *)pb;
+    const d3 *A = &g_sort_g[ia], *B = &g_sort_g[ib];
+    double va = g_sort_axis == 0 ? A->x : g_sort_axis == 1 ? A->y : A->z;
+    double vb = g_sort_axis == 0 ? B->x : g_sort_axis == 1 ? B->y : B->z;
+    if (va < vb) return -1;
+    if (va > vb) return 1;
+    return ia < ib ? -1 : (ia > ib);
+}
+
+static int32_t build_rec(oscene *s, int32_t first, int32_t count, double pad)
+{
+    int32_t id = s->n_nodes++;
+    onode *nd = &s->nodes[id];
+    d3 lo = mk(INFINITY, INFINITY, INFINITY), hi = mk(-INFINITY, -INFINITY, -INFINITY);
+    d3 clo = lo, chi = hi;
+    for (int32_t k = first; k < first + count; k++) {
+        int32_t t = s->perm[k];
+        d3 v[3] = {s->a[t], add(s->a[t], s->e1[t]), add(s->a[t], s->e2[t])};
+        for (int q = 0; q < 3; q++) {
+            lo = mk(dmin(lo.x, v[q].x), dmin(lo.y, v[q].y), dmin(lo.z, v[q].z));
+            hi = mk(dmax(hi.x, v[q].x), dmax(hi.y, v[q].y), dmax(hi.z, v[q].z));
+        }
+        clo = mk(dmin(clo.x, s->g[t].x), dmin(clo.y, s->g[t].y), dmin(clo.z, s->g[t].z));
+        chi = mk(dmax(chi.x, s->g[t].x), dmax(chi.y, s->g[t].y), dmax(chi.z, s->g[t].z));
+    }
+    nd->lo = sub(lo, mk(pad, pad, pad));
+    nd->hi = add(hi, mk(pad, pad, pad));
+    if (count <= 4) {
+        nd->first = first; nd->count = count; nd->left = nd->right = -1;
+        return id;
+    }
+    d3 ext = sub(chi, clo);
+    int axis = (ext.x >= ext.y && ext.x >= ext.z) ? 0 : (ext.y >= ext.z ? 1 : 2);
+    g_sort_g = s->g;
+    g_sort_axis = axis;
+    qsort(s->perm + first, (size_t)count, sizeof(int32_t), cmp_axis);
+    int32_t half = count / 2;
+    nd->first = first; nd->count = 0;
+    int32_t l = build_rec(s, first, half, pad);
+    int32_t r = build_rec(s, first + half, count - half, pad);
+    s->nodes[id].left = l;
+    s->nodes[id].right = r;
+    return id;
+}
+
+ORC_API void *orc_scene_create(const float *verts, int64_t nv, const int32_t *tris,
+                               int64_t nt, const float *albedo)
+{
+    (void)nv;
+    oscene *s = (oscene *)calloc(1, sizeof(oscene));
+    s->nt = nt;
+    s->a = malloc(sizeof(d3) * nt);   s->e1 = malloc(sizeof(d3) * nt);
+    s->e2 = malloc(sizeof(d3) * nt);  s->cr = malloc(sizeof(d3) * nt);
+    s->n = malloc(sizeof(d3) * nt);   s->g = malloc(sizeof(d3) * nt);
+    s->area = malloc(sizeof(double) * nt);
+    s->rho = malloc(sizeof(double) * 3 * nt);
+    s->glo = s->vlo = mk(INFINITY, INFINITY, INFINITY);
+    s->ghi = s->vhi = mk(-INFINITY, -INFINITY, -INFINITY);
+    for (int64_t t = 0; t < nt; t++) {
+        d3 a = lf3(verts + 3 * (int64_t)tris[3 * t + 0]);
+        d3 b = lf3(verts + 3 * (int64_t)tris[3 * t + 1]);
+        d3 c = lf3(verts + 3 * (int64_t)tris[3 * t + 2]);
+        d3 e1 = sub(b, a), e2 = sub(c, a);
+        d3 cr = cross(e1, e2);
+        double l = len(cr);
+        s->a[t] = a; s->e1[t] = e1; s->e2[t] = e2; s->cr[t] = cr;
+        s->n[t] = l > 0.0 ? mk(cr.x / l, cr.y / l, cr.z / l) : mk(0, 0, 0);
+        s->area[t] = 0.5 * l;
+        d3 g = add(add(a, b), c);
+        s->g[t] = mk(g.x / 3.0, g.y / 3.0, g.z / 3.0);
+        for (int k = 0; k < 3; k++) s->rho[3 * t + k] = (double)albedo[3 * t + k];
+        d3 gg = s->g[t];
+        s->glo = mk(dmin(s->glo.x, gg.x), dmin(s->glo.y, gg.y), dmin(s->glo.z, gg.z));
+        s->ghi = mk(dmax(s->ghi.x, gg.x), dmax(s->ghi.y, gg.y), dmax(s->ghi.z, gg.z));
+        d3 vv[3] = {a, b, c};
+        for (int q = 0; q < 3; q++) {
+            s->vlo = mk(dmin(s->vlo.x, vv[q].x), dmin(s->vlo.y, vv[q].y), dmin(s->vlo.z, vv[q].z));
+            s->vhi = mk(dmax(s->vhi.x, vv[q].x), dmax(s->vhi.y, vv[q].y), dmax(s->vhi.z, vv[q].z));
+        }
+    }
+    /* BVH */
+    s->perm = malloc(sizeof(int32_t) * (nt > 0 ? nt : 1));
+    for (int64_t t = 0; t < nt; t++) s->perm[t] = (int32_t)t;
+    s->nodes = malloc(sizeof(onode) * (2 * (nt > 0 ? nt : 1)));
+    s->n_nodes = 0;
+    double pad = 1e-9 * (len(sub(s->vhi, s->vlo)) + 1.0);
+    if (nt > 0) build_rec(s, 0, (int32_t)nt, pad);
+    return s;
+}
+
+ORC_API void orc_scene_destroy(void *p)
+{
+    oscene *s = (oscene *)p;
+    if (!s) return;
+    free(s->a); free(s->e1); free(s->e2); free(s->cr); free(s->n); free(s->g);
+    free(s->area); free(s->rho); free(s->nodes); free(s->perm);
+    free(s);
+}
+
+ORC_API void orc_scene_info(void *p, double out[14])
+{
+    oscene *s = (oscene *)p;
+    st3(out + 0, s->glo); st3(out + 3, s->ghi);
+    st3(out + 6, s->vlo); st3(out + 9, s->vhi);
+    out[12] = (double)s->n_nodes;
+    out[13] = (double)s->nt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ray / triangle (Moller-Trumbore, inclusive barycentric bounds)           */
+/* ------------------------------------------------------------------------ */
+/* returns 1 and t when the line o + t d meets triangle k (either side) */
+static int tri_hit(const oscene *s, int64_t k, d3 o, d3 d, double *t_out)
+{
+    d3 pv = cross(d, s->e2[k]);
+    double det = dot(s->e1[k], pv);
+    if (det == 0.0) return 0;
+    double inv = 1.0 / det;
+    d3 tv = sub(o, s->a[k]);
+    double u = dot(tv, pv) * inv;
+    if (u < 0.0 || u > 1.0) return 0;
+    d3 qv = cross(tv, s->e1[k]);
+    double v = dot(d, qv) * inv;
+    if (v < 0.0 || u + v > 1.0) return 0;
+    *t_out = dot(s->e2[k], qv) * inv;
+    return 1;
+}
+
+/* slab test of the ray against a (padded) box, interval [t0, t1] */
+static int box_hit(const onode *nd, d3 o, d3 d, double t0, double t1, double *t_enter)
+{
+    double lo[3] = {nd->lo.x, nd->lo.y, nd->lo.z}, hi[3] = {nd->hi.x, nd->hi.y, nd->hi.z};
+    double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+    for (int a = 0; a < 3; a++) {
+        if (dd[a] == 0.0) {
+            if (oo[a] < lo[a] || oo[a] > hi[a]) return 0;
+            continue;
+        }
+        double ta = (lo[a] - oo[a]) / dd[a], tb = (hi[a] - oo[a]) / dd[a];
+        if (ta > tb) { double tmp = ta; ta = tb; tb = tmp; }
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+        if (t0 > t1) return 0;
+    }
+    *t_enter = t0;
+    return 1;
+}
+
+/* closest hit with t > tmin; ties broken by the lower triangle index */
+static int64_t closest_brute(const oscene *s, d3 o, d3 d, double tmin, double *t_best)
+{
+    int64_t best = -1;
+    double bt = INFINITY, t;
+    for (int64_t k = 0; k < s->nt; k++)
+        if (tri_hit(s, k, o, d, &t) && t > tmin && t < bt) { bt = t; best = k; }
+    *t_best = bt;
+    return best;
+}
+
+static int64_t closest_bvh(const oscene *s, d3 o, d3 d, double tmin, double *t_best)
+{
+    int64_t best = -1;
+    double bt = INFINITY;
+    if (s->nt == 0) { *t_best = bt; return -1; }
+    int32_t stack[128];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const onode *nd = &s->nodes[stack[--sp]];
+        double te;
+        if (!box_hit(nd, o, d, tmin, bt, &te)) continue;
+        if (nd->count > 0) {
+            for (int32_t q = nd->first; q < nd->first + nd->count; q++) {
+                int64_t k = s->perm[q];
+                double t;
+                if (tri_hit(s, k, o, d, &t) && t > tmin &&
+                    (t < bt || (t == bt && k < best))) { bt = t; best = k; }
+            }
+        } else {
+            stack[sp++] = nd->left;
+            stack[sp++] = nd->right;
+        }
+    }
+    *t_best = bt;
+    return best;
+}
+
+/* segment p -> q blocked by any triangle at t in (0, 1), either side */
+static int occluded_brute(const oscene *s, d3 p, d3 q)
+{
+    d3 d = sub(q, p);
+    double t;
+    for (int64_t k = 0; k < s->nt; k++)
+        if (tri_hit(s, k, p, d, &t) && t > 0.0 && t < 1.0) return 1;
+    return 0;
+}
+
+static int occluded_bvh(const oscene *s, d3 p, d3 q)
+{
+    if (s->nt == 0) return 0;
+    d3 d = sub(q, p);
+    int32_t stack[128];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const onode *nd = &s->nodes[stack[--sp]];
+        double te;
+        if (!box_hit(nd, p, d, 0.0, 1.0, &te)) continue;
+        if (nd->count > 0) {
+            for (int32_t k = nd->first; k < nd->first + nd->count; k++) {
+                double t;
+                if (tri_hit(s, s->perm[k], p, d, &t) && t > 0.0 && t < 1.0) return 1;
+            }
+        } else {
+            stack[sp++] = nd->left;
+            stack[sp++] = nd->right;
+        }
+    }
+    return 0;
+}
+
+static int64_t closest(const oscene *s, d3 o, d3 d, double tmin, double *t, int vis_mode)
+{
+    return vis_mode == 1 ? closest_brute(s, o, d, tmin, t) : closest_bvh(s, o, d, tmin, t);
+}
+static int occluded(const oscene *s, d3 p, d3 q, int vis_mode)
+{
+    return vis_mode == 1 ? occluded_brute(s, p, q) : occluded_bvh(s, p, q);
+}
+
+ORC_API void orc_closest_batch(void *sp, int64_t n, const double *o, const double *d,
+                               double tmin, int32_t vis_mode, int64_t *tri, double *t)
+{
+    const oscene *s = (const oscene *)sp;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++)
+        tri[i] = closest(s, ld3(o + 3 * i), ld3(d + 3 * i), tmin, &t[i], vis_mode);
+}
+
+ORC_API void orc_occluded_batch(void *sp, int64_t n, const double *p, const double *q,
+                                int32_t vis_mode, uint8_t *out)
+{
+    const oscene *s = (const oscene *)sp;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++)
+        out[i] = (uint8_t)occluded(s, ld3(p + 3 * i), ld3(q + 3 * i), vis_mode);
+}
+
+/* Smallest distance-like margin of segment p->q to flipping its visibility:
+ * for every triangle whose plane the segment crosses (or nearly touches), the
+ * distance of the crossing point to the triangle's boundary, and the
+ * distance of the endpoints to the plane.  A GPU/oracle visibility
+ * disagreement is explained when this margin is tiny. */
+ORC_API double orc_segment_margin(void *sp, const double *p3, const double *q3)
+{
+    const oscene *s = (const oscene *)sp;
+    d3 p = ld3(p3), q = ld3(q3), d = sub(q, p);
+    double best = INFINITY;
+    for (int64_t k = 0; k < s->nt; k++) {
+        double nl = len(s->cr[k]);
+        if (nl == 0.0) continue;
+        d3 nn = scl(s->cr[k], 1.0 / nl);
+        double sp_ = dot(sub(p, s->a[k]), nn), sq_ = dot(sub(q, s->a[k]), nn);
+        /* endpoint close to the plane and over the triangle */
+        double dd = dot(d, nn);
+        if (fabs(dd) == 0.0) continue;
+        double t = -sp_ / dd;
+        if (t < -1e-3 || t > 1.0 + 1e-3) {
+            continue;
+        }
+        d3 x = add(p, scl(d, t));
+        /* distance of x to the triangle's edges (in-plane, signed inside > 0) */
+        d3 v0 = s->a[k], v1 = add(v0, s->e1[k]), v2 = add(v0, s->e2[k]);
+        d3 vs[3] = {v0, v1, v2};
+        double m_in = INFINITY;
+        for (int e = 0; e < 3; e++) {
+            d3 A = vs[e], B = vs[(e + 1) % 3];
+            d3 ed = sub(B, A);
+            d3 inw = cross(nn, ed);
+            double il = len(inw);
+            if (il == 0.0) continue;
+            double sd = dot(sub(x, A), inw) / il;
+            if (fabs(sd) < m_in) m_in = fabs(sd);
+        }
+        int inside = 1;
+        for (int e = 0; e < 3; e++) {
+            d3 A = vs[e], B = vs[(e + 1) % 3];
+            if (dot(cross(sub(B, A), sub(x, A)), nn) < 0.0) inside = 0;
+        }
+        double m = m_in;
+        if (inside) {
+            double ep = dmin(fabs(sp_), fabs(sq_));
+            if (ep < m) m = ep;
+        }
+        if (m < best) best = m;
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* camera frame and close-range classification                              */
+/* ------------------------------------------------------------------------ */
+typedef struct { d3 e, f, r, u; double tv, th; } frame;
+
+static frame cam_frame(const ocamera *c)
+{
+    frame F;
+    F.e = ld3(c->eye);
+    F.f = unit(ld3(c->fwd));
+    F.r = unit(cross(F.f, ld3(c->up)));
+    F.u = cross(F.r, F.f);
+    F.tv = tan(c->vfov_deg * (PI / 180.0) * 0.5);
+    F.th = (F.tv * (double)c->width) / (double)c->height;
+    return F;
+}
+
+/* close/distant split: a one-sided face is close range when it faces the
+ * camera, lies inside the field of view and nearer than d_close; patch
+ * sampling further only considers faces that face the light. */
+static int is_close(const oscene *s, int64_t t, const frame *F, const olight *L, double dc2)
+{
+    d3 g = s->g[t], cr = s->cr[t];
+    if (!(dot(cr, sub(F->e, g)) > 0.0)) return 0;
+    d3 v = sub(g, F->e);
+    double z = dot(v, F->f);
+    if (!(z > 0.0)) return 0;
+    if (!(fabs(dot(v, F->r)) <= z * F->th)) return 0;
+    if (!(fabs(dot(v, F->u)) <= z * F->tv)) return 0;
+    if (!(dot(v, v) < dc2)) return 0;
+    d3 cl = ld3(L->center);
+    if (!(dot(cr, sub(cl, g)) > 0.0)) return 0;
+    if (L->type == 0 && !(dot(ld3(L->normal), sub(g, cl)) > 0.0)) return 0;
+    return 1;
+}
+
+ORC_API int64_t orc_classify(void *sp, const ocamera *cam, const olight *L, double d_close,
+                             uint8_t *flags)
+{
+    const oscene *s = (const oscene *)sp;
+    frame F = cam_frame(cam);
+    double dc2 = d_close * d_close;
+    int64_t n = 0;
+    for (int64_t t = 0; t < s->nt; t++) {
+        flags[t] = (uint8_t)is_close(s, t, &F, L, dc2);
+        n += flags[t];
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* light sampling and hemisphere directions                                 */
+/* ------------------------------------------------------------------------ */
+static d3 light_point(const olight *L, double s1, double s2)
+{
+    d3 c = ld3(L->center);
+    if (L->type == 1) return c;
+    d3 a = scl(ld3(L->edge_u), (2.0 * s1 - 1.0) * 0.5);
+    d3 b = scl(ld3(L->edge_v), (2.0 * s2 - 1.0) * 0.5);
+    return add(add(c, a), b);
+}
+
+/* orthonormal basis around unit n (Duff et al., JCGT 2017) */
+static void onb(d3 n, d3 *t1, d3 *t2)
+{
+    double sg = copysign(1.0, n.z);
+    double a = -1.0 / (sg + n.z);
+    double b = n.x * n.y * a;
+    *t1 = mk(1.0 + sg * n.x * n.x * a, sg * b, -sg * n.x);
+    *t2 = mk(b, sg + n.y * n.y * a, -n.y);
+}
+
+/* cosine-weighted direction about n (Malley's method) */
+static d3 cosine_dir(d3 n, double s1, double s2)
+{
+    d3 t1, t2;
+    onb(n, &t1, &t2);
+    double r = sqrt(s1), ph = 2.0 * PI * s2;
+    return add(add(scl(t1, r * cos(ph)), scl(t2, r * sin(ph))), scl(n, sqrt(1.0 - s1)));
+}
+
+static d3 sphere_dir(double s1, double s2)
+{
+    double z = 1.0 - 2.0 * s1;
+    double r = sqrt(dmax(0.0, 1.0 - z * z)), ph = 2.0 * PI * s2;
+    return mk(r * cos(ph), r * sin(ph), z);
+}
+
+/* ------------------------------------------------------------------------ */
+/* VPL generation (pipeline steps (1)-(3))                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_close;     /* |C|                                  */
+    int64_t shift_s;     /* S in q_t = llround(A_t 2^S)          */
+    uint64_t f_total;    /* f(N) in quantised units              */
+    int64_t paths;       /* P                                    */
+    int64_t m_far_kept;  /* far VPLs produced (< m_far if exhausted) */
+    double a_rep;        /* area represented by one patch VPL    */
+    int64_t status;      /* 0 ok, 6 close set empty, 7 paths exhausted */
+} oinfo;
+
+typedef struct { uint64_t code; int32_t tri; } mkey;
+static int cmp_mkey(const void *pa, const void *pb)
+{
+    const mkey *a = (const mkey *)pa, *b = (const mkey *)pb;
+    if (a->code != b->code) return a->code < b->code ? -1 : 1;
+    return a->tri < b->tri ? -1 : (a->tri > b->tri);
+}
+
+/* Eq. 2 for a VPL at x (unit normal n, albedo rho, area D): reflected power */
+static d3 patch_flux(const oscene *s, const olight *L, const ogen *G, int64_t k, d3 x, d3 n,
+                     const double *rho, double D)
+{
+    d3 cl = ld3(L->center), P = ld3(L->power);
+    d3 xo = add(x, scl(n, G->ray_eps));
+    double acc = 0.0;
+    if (L->type == 1) {
+        /* Eq. 2 literally: G = D cos(w) / (4 pi r^2), w and r towards the light */
+        d3 dv = sub(cl, x);
+        double r = len(dv);
+        double cw = dot(n, dv) / r;
+        if (cw > 0.0 && !occluded(s, xo, cl, G->vis_mode))
+            acc = D * cw / (4.0 * PI * r * r);
+    } else {
+        /* one-sided Lambertian square of power P: radiance P / (pi A_L);
+         * incident power on area D estimated with light_samples points */
+        d3 nl = ld3(L->normal);
+        for (int32_t sidx = 0; sidx < G->light_samples; sidx++) {
+            uint64_t w[4];
+            rng4(G->seed, STREAM_LIGHT, (uint64_t)k, (uint64_t)sidx, w);
+            d3 y = light_point(L, u01(w[0]), u01(w[1]));
+            d3 dv = sub(y, x);
+            double r2 = dot(dv, dv), r = sqrt(r2);
+            double cw = dot(n, dv) / r;
+            double cl_ = -dot(nl, dv) / r;
+            if (cw > 0.0 && cl_ > 0.0 && !occluded(s, xo, y, G->vis_mode))
+                acc += cw * cl_ / (PI * r2);
+        }
+        acc = D * acc / (double)G->light_samples;
+    }
+    return mk(rho[0] * P.x * acc, rho[1] * P.y * acc, rho[2] * P.z * acc);
+}
+
+ORC_API int64_t orc_generate(void *sp, const ocamera *cam, const olight *L, const ogen *G,
+                             double *pos, double *nrm, double *flux, int64_t *tri,
+                             int64_t *tag, oinfo *info)
+{
+    const oscene *s = (const oscene *)sp;
+    memset(info, 0, sizeof(*info));
+    const int64_t M = (int64_t)G->m_close + G->m_far;
+    for (int64_t i = 0; i < 3 * M; i++) pos[i] = nrm[i] = flux[i] = 0.0;
+    for (int64_t i = 0; i < M; i++) { tri[i] = -1; tag[i] = -1; }
+
+    /* (1) close-range faces */
+    uint8_t *close = calloc((size_t)(s->nt > 0 ? s->nt : 1), 1);
+    int64_t nc = orc_classify(sp, cam, L, G->d_close, close);
+    info->n_close = nc;
+
+    /* (2) patch sampling of the close range */
+    if (G->m_close > 0) {
+        if (nc == 0) {
+            info->status = 6;
+        } else {
+            /* spatial order: Morton code of the centroid in the AABB of all
+             * centroids, ties by triangle index */
+            mkey *keys = malloc(sizeof(mkey) * nc);
+            int64_t j = 0;
+            for (int64_t t = 0; t < s->nt; t++) {
+                if (!close[t]) continue;
+                d3 g = s->g[t];
+                keys[j].code = orc_morton63(quant21(g.x, s->glo.x, s->ghi.x),
+                                            quant21(g.y, s->glo.y, s->ghi.y),
+                                            quant21(g.z, s->glo.z, s->ghi.z));
+                keys[j].tri = (int32_t)t;
+                j++;
+            }
+            qsort(keys, (size_t)nc, sizeof(mkey), cmp_mkey);
+            /* integer areas q_t = round(A_t 2^S) with S = 40 - exponent(max A) */
+            double amax = 0.0;
+            for (int64_t i = 0; i < nc; i++) amax = dmax(amax, s->area[keys[i].tri]);
+            int ex;
+            frexp(amax, &ex);
+            int S = 40 - ex;
+            info->shift_s = S;
+            /* f(i): area prefix sum over the sorted list, f[0] = 0 */
+            uint64_t *f = malloc(sizeof(uint64_t) * (nc + 1));
+            f[0] = 0;
+            for (int64_t i = 0; i < nc; i++)
+                f[i + 1] = f[i] + (uint64_t)llround(ldexp(s->area[keys[i].tri], S));
+            uint64_t F = f[nc];
+            info->f_total = F;
+            const uint64_t K = (uint64_t)G->m_close;
+            double a_rep = ldexp((double)F, -S) / (double)K;
+            info->a_rep = a_rep;
+            for (uint64_t k = 0; k < K; k++) {
+                uint64_t w[4];
+                rng4(G->seed, STREAM_PATCH, k, 0, w);
+                /* a point in stratum [kF/K, (k+1)F/K) */
+                unsigned __int128 num = ((unsigned __int128)((k << 32) + (w[0] >> 32))) * F;
+                uint64_t u = (uint64_t)(num / ((unsigned __int128)K << 32));
+                /* g(u): index m with f(m) <= u < f(m+1) */
+                int64_t lo = 0, hi = nc;   /* invariant f[lo] <= u < f[hi] */
+                while (hi - lo > 1) {
+                    int64_t mid = lo + (hi - lo) / 2;
+                    if (f[mid] <= u) lo = mid; else hi = mid;
+                }
+                int64_t t = keys[lo].tri;
+                /* uniform random point in triangle t */
+                double r1 = u01(w[1]), r2 = u01(w[2]);
+                double sr = sqrt(r1);
+                d3 a = s->a[t], b = add(a, s->e1[t]), c = add(a, s->e2[t]);
+                d3 x = add(add(scl(a, 1.0 - sr), scl(b, sr * (1.0 - r2))), scl(c, sr * r2));
+                d3 fl = patch_flux(s, L, G, (int64_t)k, x, s->n[t], s->rho + 3 * t, a_rep);
+                st3(pos + 3 * k, x);
+                st3(nrm + 3 * k, s->n[t]);
+                st3(flux + 3 * k, fl);
+                tri[k] = t;
+                tag[k] = (int64_t)k;
+            }
+            free(f);
+            free(keys);
+        }
+    }
+
+    /* (3) instant radiosity over the whole scene; only hits on the distant
+     * part become VPLs, hits on the close range are discarded but the path
+     * goes on */
+    if (G->m_far > 0) {
+        const int64_t base = G->m_close;
+        int64_t kept = 0, p = 0, P = 0;
+        d3 nl = ld3(L->normal);
+        const int64_t pmax = G->ir_max_paths;
+        while (kept < G->m_far && p < pmax) {
+            uint64_t w[4];
+            rng4(G->seed, STREAM_IR, (uint64_t)p, 0, w);
+            d3 o, d;
+            if (L->type == 1) {
+                o = ld3(L->center);
+                d = sphere_dir(u01(w[2]), u01(w[3]));
+            } else {
+                o = light_point(L, u01(w[0]), u01(w[1]));
+                d = cosine_dir(nl, u01(w[2]), u01(w[3]));
+            }
+            double thr[3] = {1.0, 1.0, 1.0};
+            for (int32_t b = 1; b <= G->max_bounces && kept < G->m_far; b++) {
+                double t;
+                int64_t k = closest(s, o, d, 0.0, &t, G->vis_mode);
+                if (k < 0) break;
+                if (!(dot(d, s->cr[k]) < 0.0)) break;   /* back face absorbs */
+                d3 x = add(o, scl(d, t));
+                for (int c = 0; c < 3; c++) thr[c] = thr[c] * s->rho[3 * k + c];
+                if (!close[k]) {
+                    int64_t i = base + kept;
+                    st3(pos + 3 * i, x);
+                    st3(nrm + 3 * i, s->n[k]);
+                    st3(flux + 3 * i, mk(thr[0], thr[1], thr[2]));
+                    tri[i] = k;
+                    tag[i] = p * 16 + b;
+                    kept++;
+                    P = p + 1;
+                }
+                if (b == G->max_bounces) break;
+                rng4(G->seed, STREAM_IR, (uint64_t)p, (uint64_t)b, w);
+                d = cosine_dir(s->n[k], u01(w[0]), u01(w[1]));
+                o = add(x, scl(s->n[k], G->ray_eps));
+            }
+            p++;
+        }
+        if (kept < G->m_far) { info->status = 7; P = pmax; }
+        info->paths = P;
+        info->m_far_kept = kept;
+        d3 pw = ld3(L->power);
+        for (int64_t i = 0; i < kept; i++) {
+            double *fl = flux + 3 * (base + i);
+            fl[0] = pw.x * fl[0] / (double)P;
+            fl[1] = pw.y * fl[1] / (double)P;
+            fl[2] = pw.z * fl[2] / (double)P;
+        }
+    }
+    free(close);
+    return info->status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* G-buffer: closest front-face hit through each requested pixel centre      */
+/* ------------------------------------------------------------------------ */
+ORC_API void orc_gbuffer(void *sp, const ocamera *cam, int64_t n, const int64_t *pix,
+                         int32_t vis_mode, double *pos, double *nrm, double *rho, int64_t *tri)
+{
+    const oscene *s = (const oscene *)sp;
+    frame F = cam_frame(cam);
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < n; q++) {
+        int64_t i = pix[q] % cam->width, j = pix[q] / cam->width;
+        double sx = 2.0 * ((double)i + 0.5) / (double)cam->width - 1.0;
+        double sy = 1.0 - 2.0 * ((double)j + 0.5) / (double)cam->height;
+        d3 d = add(add(F.f, scl(F.r, sx * F.th)), scl(F.u, sy * F.tv));
+        double t;
+        int64_t k = closest(s, F.e, d, 0.0, &t, vis_mode);
+        if (k >= 0 && dot(d, s->cr[k]) < 0.0) {
+            st3(pos + 3 * q, add(F.e, scl(d, t)));
+            st3(nrm + 3 * q, s->n[k]);
+            for (int c = 0; c < 3; c++) rho[3 * q + c] = s->rho[3 * k + c];
+            tri[q] = k;
+        } else {
+            st3(pos + 3 * q, mk(0, 0, 0));
+            st3(nrm + 3 * q, mk(0, 0, 0));
+            for (int c = 0; c < 3; c++) rho[3 * q + c] = 0.0;
+            tri[q] = -1;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gather (Eq. 1, indirect part): every pixel sums all VPLs in index order   */
+/* ------------------------------------------------------------------------ */
+/* shading factor of one pair without visibility and without the receiver's
+ * albedo: cos_i cos_y / (pi max(d^2, d2_min)) */
+static double pair_term(d3 y, d3 ny, d3 x, d3 nx, double d2min)
+{
+    d3 d = sub(x, y);
+    double d2 = dot(d, d);
+    if (d2 == 0.0) return 0.0;
+    double dl = sqrt(d2);
+    double cy = dot(ny, d) / dl;
+    double ci = -dot(nx, d) / dl;
+    if (!(cy > 0.0) || !(ci > 0.0)) return 0.0;
+    return ci * cy / (PI * dmax(d2, d2min));
+}
+
+ORC_API void orc_gather(void *sp, int64_t n, const double *y, const double *ny,
+                        const double *rho, const int64_t *valid, int64_t M, const double *x,
+                        const double *nx, const double *phi, double d2min, double eps,
+                        int32_t vis_mode, double *out)
+{
+    const oscene *s = (const oscene *)sp;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < n; q++) {
+        double L[3] = {0.0, 0.0, 0.0};
+        if (valid[q] >= 0) {
+            d3 yy = ld3(y + 3 * q), nyy = ld3(ny + 3 * q);
+            d3 p = add(yy, scl(nyy, eps));
+            for (int64_t i = 0; i < M; i++) {
+                const double *fi = phi + 3 * i;
+                if (fi[0] == 0.0 && fi[1] == 0.0 && fi[2] == 0.0) continue;
+                d3 xi = ld3(x + 3 * i), ni = ld3(nx + 3 * i);
+                double g = pair_term(yy, nyy, xi, ni, d2min);
+                if (g == 0.0) continue;
+                if (vis_mode != 2 && occluded(s, p, add(xi, scl(ni, eps)), vis_mode)) continue;
+                for (int c = 0; c < 3; c++) L[c] = L[c] + fi[c] * g;
+            }
+        }
+        for (int c = 0; c < 3; c++) out[3 * q + c] = rho[3 * q + c] / PI * L[c];
+    }
+}
+
+/* Per-pair shading factor and visibility for one receiver, for flip
+ * analysis: term[i] (no visibility), vis[i] (1 visible, 0 blocked, -1 not
+ * traced because term is zero), margin[i] (orc_segment_margin, only where
+ * want_margin[i] != 0). */
+ORC_API void orc_pairs(void *sp, const double *y, const double *ny, int64_t M, const double *x,
+                       const double *nx, double d2min, double eps, int32_t vis_mode,
+                       const uint8_t *want_margin, double *term, int8_t *vis, double *margin)
+{
+    const oscene *s = (const oscene *)sp;
+    d3 yy = ld3(y), nyy = ld3(ny);
+    d3 p = add(yy, scl(nyy, eps));
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < M; i++) {
+        d3 xi = ld3(x + 3 * i), ni = ld3(nx + 3 * i);
+        term[i] = pair_term(yy, nyy, xi, ni, d2min);
+        d3 q = add(xi, scl(ni, eps));
+        vis[i] = term[i] == 0.0 ? -1 : (int8_t)!occluded(s, p, q, vis_mode);
+        margin[i] = INFINITY;
+        if (want_margin && want_margin[i]) {
+            double pp[3] = {p.x, p.y, p.z}, qq[3] = {q.x, q.y, q.z};
+            margin[i] = orc_segment_margin(sp, pp, qq);
+        }
+    }
+}
+
+ORC_API int32_t orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

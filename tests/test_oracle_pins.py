@@ -1,0 +1,513 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed forms, invariants, library routines, brute force).  CPU only.
+
+Each test names the passage of the paper (Jin et al., arXiv 2203.11484) it
+pins and what independent fact it uses.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2203_11484_gb300 import workloads as W
+
+F32 = np.float32
+
+
+def tri_scene(verts, tris, albedo, light=None):
+    verts = np.asarray(verts, np.float32)
+    tris = np.asarray(tris, np.int32)
+    albedo = np.broadcast_to(np.asarray(albedo, np.float32), (tris.shape[0], 3)).copy()
+    if light is None:
+        light = W.Light(center=(0.0, 0.0, 10.0), normal=(0.0, 0.0, -1.0),
+                        edge_u=(1.0, 0.0, 0.0), edge_v=(0.0, 1.0, 0.0), type=W.LIGHT_POINT)
+    return W.Scene(verts, tris, albedo, light)
+
+
+def plane_scene(half=10.0, z=0.0, up=True, albedo=0.5, light=None):
+    """Square [-half, half]^2 at height z, facing +z (or -z)."""
+    v = [(-half, -half, z), (half, -half, z), (half, half, z), (-half, half, z)]
+    t = [(0, 1, 2), (0, 2, 3)] if up else [(0, 2, 1), (0, 3, 2)]
+    return tri_scene(v, t, albedo, light)
+
+
+def closed_box_scene(albedo=0.5, n=2):
+    s = W._Soup()
+    W._room_zup(s, (1.0, 1.0, 1.0), n, n, n, albedo_fn=lambda: (albedo,) * 3)
+    light = W.Light(center=(0.5, 0.5, 1.0 - 1e-3), normal=(0.0, 0.0, -1.0),
+                    edge_u=(0.2, 0.0, 0.0), edge_v=(0.0, 0.2, 0.0), type=W.LIGHT_AREA)
+    return s.finish(light)
+
+
+# ---------------------------------------------------------------------------
+# Philox4x64-10: library routine (numpy ships the same generator)
+# ---------------------------------------------------------------------------
+def _numpy_philox_block(ctr, key):
+    """numpy increments its 256-bit counter before producing a block, so the
+    block for counter c is produced from state c - 1."""
+    c = sum(int(ctr[i]) << (64 * i) for i in range(4))
+    k = int(key[0]) | (int(key[1]) << 64)
+    bg = np.random.Philox(key=k, counter=(c - 1) % (1 << 256))
+    return bg.random_raw(4)
+
+
+def test_philox_matches_numpy(orc):
+    rng = np.random.default_rng(123)
+    cases = [((0, 0, 0, 0), (0, 0)), ((1, 0, 0, 0), (0, 1)), ((5, 7, 0, 0), (99, 3)),
+             ((2**64 - 1, 2**64 - 1, 2**64 - 1, 2**64 - 1), (2**64 - 1, 2**64 - 1))]
+    for _ in range(300):
+        cases.append((tuple(int(x) for x in rng.integers(0, 2**63, 4, dtype=np.uint64)),
+                      tuple(int(x) for x in rng.integers(0, 2**63, 2, dtype=np.uint64))))
+    for ctr, key in cases:
+        got = orc.philox4x64_10(ctr, key)
+        want = _numpy_philox_block(ctr, key)
+        assert np.array_equal(got, want), (ctr, key)
+
+
+# ---------------------------------------------------------------------------
+# Morton order (Sec. 3, "Realization": spatial sort by Morton code)
+# ---------------------------------------------------------------------------
+def test_morton_bit_interleave(orc):
+    assert orc.morton63(1, 0, 0) == 4
+    assert orc.morton63(0, 1, 0) == 2
+    assert orc.morton63(0, 0, 1) == 1
+    m = 2**21 - 1
+    assert orc.morton63(m, m, m) == 2**63 - 1
+    rng = np.random.default_rng(7)
+    for _ in range(500):
+        q = [int(v) for v in rng.integers(0, 2**21, 3)]
+        # independent restatement: read the bits of the code back out
+        code = orc.morton63(*q)
+        back = [0, 0, 0]
+        for bit in range(63):
+            if code >> bit & 1:
+                axis = 2 - bit % 3
+                back[axis] |= 1 << (bit // 3)
+        assert back == q
+
+
+# ---------------------------------------------------------------------------
+# close/distant split (Sec. 3): one-sided, in the field of view, nearer than a
+# threshold; patch sampling only on faces facing the light
+# ---------------------------------------------------------------------------
+def _cam(eye=(0, 0, 0), fwd=(0, 0, 1), up=(0, 1, 0), w=64, h=64, vfov=60.0):
+    return W.Camera(eye=eye, forward=fwd, up=up, vfov_deg=vfov, width=w, height=h)
+
+
+def test_classify_hand_cases(orc):
+    light = W.Light(center=(0.0, 0.0, -1.0), normal=(0.0, 0.0, 1.0), edge_u=(0.1, 0, 0),
+                    edge_v=(0, 0.1, 0), type=W.LIGHT_POINT)
+    s = 0.1
+    def facing_cam(cx, cy, cz):   # triangle facing -z (towards a camera at the origin)
+        return [(cx - s, cy - s, cz), (cx, cy + s, cz), (cx + s, cy - s, cz)]
+    tris_v = [
+        facing_cam(0, 0, 1),          # 0 close
+        facing_cam(0, 0, 10),         # 1 beyond the threshold
+        facing_cam(5, 0, 1),          # 2 outside the horizontal field of view
+        facing_cam(0, 5, 1),          # 3 outside the vertical field of view
+        facing_cam(0, 0, -1),         # 4 behind the camera
+        list(reversed(facing_cam(0, 0, 1.5))),  # 5 back face towards the camera
+        facing_cam(0.4, 0.4, 1.0),    # 6 inside (corner of the frustum, tan 30deg = 0.577)
+    ]
+    verts = np.array([p for t in tris_v for p in t], np.float32)
+    tris = np.arange(len(verts)).reshape(-1, 3)
+    sc = tri_scene(verts, tris, 0.5, light)
+    o = orc.OracleScene(sc)
+    got = o.classify(_cam(), 3.0)
+    assert got.tolist() == [True, False, False, False, False, False, True]
+    # the light behind the faces: nothing faces it
+    sc2 = tri_scene(verts, tris, 0.5, W.Light(center=(0.0, 0.0, 20.0), normal=(0, 0, -1),
+                                             edge_u=(1, 0, 0), edge_v=(0, 1, 0),
+                                             type=W.LIGHT_POINT))
+    assert not orc.OracleScene(sc2).classify(_cam(), 3.0).any()
+    # wider screen widens the horizontal field of view only
+    wide = _cam(w=256, h=64)
+    v2 = np.array(facing_cam(1.5, 0, 1), np.float32)
+    sc3 = tri_scene(v2, [(0, 1, 2)], 0.5, light)
+    assert orc.OracleScene(sc3).classify(wide, 3.0).tolist() == [True]
+    assert orc.OracleScene(sc3).classify(_cam(), 3.0).tolist() == [False]
+
+
+def test_cornell_close_fraction(orc):
+    wl = W.cornell_workload()
+    o = orc.OracleScene(wl.scene)
+    fl = o.classify(wl.views[0].camera, wl.views[0].gen.d_close)
+    V = wl.scene.verts.astype(np.float64)
+    T = wl.scene.tris
+    A = 0.5 * np.linalg.norm(np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]]), axis=1)
+    frac = A[fl].sum() / A.sum()
+    assert fl.sum() == 8 and 0.10 <= frac <= 0.20
+
+
+# ---------------------------------------------------------------------------
+# patch strata (Sec. 3, "Realization"): K equal-area strata over f, each VPL
+# represents the same area; a big triangle gets several VPLs
+# ---------------------------------------------------------------------------
+def _areas(scene):
+    V = scene.verts.astype(np.float64)
+    T = scene.tris
+    return 0.5 * np.linalg.norm(np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]]), axis=1)
+
+
+@pytest.mark.parametrize("m_close", [1, 7, 192, 1000])
+def test_strata_counts_and_uniform_area(orc, m_close):
+    wl = W.cornell_workload()
+    v = wl.views[0]
+    o = orc.OracleScene(wl.scene)
+    gen = W.GenParams(**{**v.gen.__dict__, "m_close": m_close, "m_far": 0})
+    g = o.generate(v.camera, gen, vis_mode=1)
+    close = o.classify(v.camera, gen.d_close)
+    A = _areas(wl.scene)
+    S = g["shift_s"]
+    q = np.array([int(np.rint(np.ldexp(a, S))) for a in A])   # numpy rint: half-even,
+    # differs from llround only on exact .5 ties which cannot occur for these areas
+    F = int(q[close].sum())
+    assert g["f_total"] == F
+    counts = np.bincount(g["tri"], minlength=len(A))
+    # an interval of L strata (jittered: one uniform point per stratum) holds
+    # at least floor(L) - 1 and at most ceil(L) + 1 of the points
+    for t in np.nonzero(close)[0]:
+        L = m_close * int(q[t]) / F
+        assert max(0, math.floor(L) - 1) <= counts[t] <= math.ceil(L) + 1
+    assert counts.sum() == m_close
+    assert counts[~close].sum() == 0
+    # every VPL represents the same area; together they cover the close area
+    assert abs(g["a_rep"] * m_close - A[close].sum()) <= 1e-9 * A[close].sum()
+    # the strata are contiguous in the sorted order: each triangle's VPLs form one run
+    seen, prev = set(), None
+    for t in g["tri"]:
+        if t != prev:
+            assert t not in seen
+            seen.add(t)
+            prev = t
+
+
+def test_strata_expected_counts(orc):
+    """Averaged over seeds, triangle t receives exactly K q_t / F VPLs."""
+    wl = W.cornell_workload()
+    v = wl.views[0]
+    o = orc.OracleScene(wl.scene)
+    K, n_seeds = 50, 400
+    A = _areas(wl.scene)
+    close = o.classify(v.camera, v.gen.d_close)
+    tot = np.zeros(len(A))
+    for seed in range(n_seeds):
+        gen = W.GenParams(**{**v.gen.__dict__, "m_close": K, "m_far": 0, "seed": seed})
+        g = o.generate(v.camera, gen, vis_mode=1)
+        tot += np.bincount(g["tri"], minlength=len(A))
+    want = K * A / A[close].sum() * close
+    # per-seed variance of a count is at most 1/2 (two partial strata)
+    assert np.all(np.abs(tot / n_seeds - want) <= 4 * math.sqrt(0.5 / n_seeds) + 1e-9)
+
+
+def test_points_uniform_in_triangle(orc):
+    """One close triangle, 100k strata: barycentrics valid, chi^2 over 16
+    equal-area sub-triangles (uniform point in a triangle)."""
+    v = [(-1.0, -1.0, 0.0), (1.0, -1.0, 0.0), (0.0, 1.0, 0.0)]
+    sc = tri_scene(v, [(0, 1, 2)], 0.5)
+    cam = _cam(eye=(0, 0, 3), fwd=(0, 0, -1), up=(0, 1, 0))
+    o = orc.OracleScene(sc)
+    K = 100_000
+    gen = W.GenParams(d_close=10.0, m_close=K, m_far=0, seed=11)
+    g = o.generate(cam, gen)
+    assert g["status"] == 0 and (g["tri"] == 0).all()
+    P = g["pos"]
+    a, b, c = (np.array(x) for x in v)
+    # barycentric coordinates
+    m = np.stack([b - a, c - a], axis=1)[:2]
+    uv = np.linalg.solve(m, (P[:, :2] - a[:2]).T).T
+    assert (uv >= -1e-12).all() and (uv.sum(axis=1) <= 1 + 1e-12).all()
+    assert np.abs(P[:, 2]).max() == 0.0
+    # 16 sub-triangles of a 4x4 barycentric grid
+    n = 4
+    u, w = uv[:, 0] * n, uv[:, 1] * n
+    iu, iw = np.floor(u).astype(int), np.floor(w).astype(int)
+    upper = (u - iu) + (w - iw) > 1
+    cell = (iu * n + iw) * 2 + upper
+    hist = np.bincount(cell, minlength=2 * n * n)
+    valid = [((i * n + j) * 2 + up) for i in range(n) for j in range(n) for up in (0, 1)
+             if i + j + up <= n - 1]
+    assert len(valid) == 16 and hist[valid].sum() == K
+    exp = K / 16
+    chi2 = ((hist[valid] - exp) ** 2 / exp).sum()
+    assert chi2 < 37.7     # 15 dof, p = 0.001
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2 (patch VPL value), point light: sum over patches = rho * P * Omega/(4 pi)
+# ---------------------------------------------------------------------------
+def _solid_angle(p, a, b, c):
+    """Van Oosterom & Strackee (1983): solid angle of triangle abc seen from p."""
+    A, B, C = a - p, b - p, c - p
+    la, lb, lc = np.linalg.norm(A), np.linalg.norm(B), np.linalg.norm(C)
+    num = abs(np.dot(A, np.cross(B, C)))
+    den = la * lb * lc + np.dot(A, B) * lc + np.dot(A, C) * lb + np.dot(B, C) * la
+    return 2.0 * math.atan2(num, den)
+
+
+@pytest.mark.parametrize("K,tol", [(2000, 1.5e-2), (200000, 1.5e-3)])
+def test_eq2_point_light_total_flux(orc, K, tol):
+    light = W.Light(center=(0.3, -0.2, 2.0), normal=(0, 0, -1), edge_u=(1, 0, 0),
+                    edge_v=(0, 1, 0), power=(1.0, 2.0, 0.5), type=W.LIGHT_POINT)
+    rho = np.array([0.25, 0.5, 0.75])
+    sc = plane_scene(half=1.5, albedo=rho, light=light)
+    cam = _cam(eye=(0, 0, 4), fwd=(0, 0, -1), up=(0, 1, 0), vfov=80)
+    o = orc.OracleScene(sc)
+    g = o.generate(cam, W.GenParams(d_close=100.0, m_close=K, m_far=0, seed=3))
+    assert g["status"] == 0 and g["n_close"] == 2
+    V = sc.verts.astype(np.float64)
+    p = np.array(light.center, np.float64)
+    omega = sum(_solid_angle(p, *V[t]) for t in sc.tris)
+    want = rho * np.array(light.power) * omega / (4 * math.pi)
+    got = g["flux"].sum(axis=0)
+    assert np.allclose(got, want, rtol=tol)     # about 6 sigma of the stratified estimate
+    # each VPL: D cos(w)/(4 pi r^2) * rho * P with D the uniform represented area
+    x = g["pos"]
+    d = p - x
+    r = np.linalg.norm(d, axis=1)
+    each = g["a_rep"] * (d[:, 2] / r) / (4 * math.pi * r * r)
+    assert np.allclose(g["flux"], each[:, None] * rho * np.array(light.power), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2 with a Lambertian square light: per-VPL flux -> rho * D * E(x), with E
+# Lambert's closed-form polygon-to-point irradiance
+# ---------------------------------------------------------------------------
+def _lambert_irradiance(x, n, poly, radiance):
+    """E = (L/2) sum_i angle(u_i, u_i+1) * n . unit(u_i x u_i+1), polygon seen
+    from x wound so that its emitting side faces x."""
+    u = [(q - x) / np.linalg.norm(q - x) for q in poly]
+    e = 0.0
+    for i in range(len(u)):
+        a, b = u[i], u[(i + 1) % len(u)]
+        cr = np.cross(a, b)
+        e += math.acos(np.clip(np.dot(a, b), -1, 1)) * np.dot(n, cr / np.linalg.norm(cr))
+    return 0.5 * radiance * abs(e)
+
+
+def test_eq2_area_light_matches_lambert(orc):
+    eu, ev = np.array([0.4, 0.0, 0.0]), np.array([0.0, 0.4, 0.0])
+    c = np.array([0.1, 0.2, 1.0])
+    light = W.Light(center=tuple(c), normal=(0, 0, -1), edge_u=tuple(eu), edge_v=tuple(ev),
+                    power=(2.0, 2.0, 2.0), type=W.LIGHT_AREA)
+    sc = plane_scene(half=1.0, albedo=0.6, light=light)
+    cam = _cam(eye=(0, 0, 4), fwd=(0, 0, -1), up=(0, 1, 0), vfov=80)
+    o = orc.OracleScene(sc)
+    S_L = 20000
+    g = o.generate(cam, W.GenParams(d_close=100.0, m_close=8, m_far=0, light_samples=S_L,
+                                    seed=5))
+    poly = [c - eu / 2 - ev / 2, c + eu / 2 - ev / 2, c + eu / 2 + ev / 2, c - eu / 2 + ev / 2]
+    L = 2.0 / (math.pi * 0.16)
+    for k in range(8):
+        E = _lambert_irradiance(g["pos"][k], np.array([0, 0, 1.0]), poly, L)
+        want = 0.6 * g["a_rep"] * E
+        assert abs(g["flux"][k, 0] - want) < 0.02 * want
+
+
+# ---------------------------------------------------------------------------
+# instant radiosity (Sec. 3, pipeline step (3)); flux = power x albedos / P
+# ---------------------------------------------------------------------------
+def test_ir_flux_exact_constant_albedo(orc):
+    sc = closed_box_scene(albedo=0.5)
+    cam = _cam(eye=(0.5, 0.5, 0.5), fwd=(1, 0, 0), up=(0, 0, 1))
+    o = orc.OracleScene(sc)
+    gen = W.GenParams(d_close=0.0, m_close=0, m_far=3001, max_bounces=3, seed=9, ray_eps=1e-6)
+    g = o.generate(cam, gen)
+    assert g["status"] == 0 and g["m_far_kept"] == 3001
+    P = g["paths"]
+    b = g["tag"] % 16
+    p = g["tag"] // 16
+    assert (np.diff(g["tag"]) > 0).all() and p.max() == P - 1
+    want = 0.5 ** b / P
+    assert np.array_equal(g["flux"][:, 0], want)
+    # closed room, inward faces: no path is absorbed or escapes, so every
+    # launched path leaves exactly max_bounces VPLs (the last one truncated)
+    full = np.bincount(p, minlength=P)
+    assert (full[:-1] == 3).all() and 1 <= full[-1] <= 3
+    # first-bounce VPLs carry rho * power in total
+    assert abs(g["flux"][b == 1, 0].sum() - 0.5) < 1e-12
+
+
+def test_ir_rejects_close_hits(orc):
+    wl = W.cornell_workload()
+    v = wl.views[0]
+    o = orc.OracleScene(wl.scene)
+    g = o.generate(v.camera, v.gen, vis_mode=1)
+    close = o.classify(v.camera, v.gen.d_close)
+    M_c = v.gen.m_close
+    assert g["status"] == 0
+    assert close[g["tri"][:M_c]].all()
+    assert not close[g["tri"][M_c:]].any()
+    assert len(g["tri"]) == M_c + v.gen.m_far
+    # far VPLs lie on their triangle's plane
+    V = wl.scene.verts.astype(np.float64)
+    T = wl.scene.tris[g["tri"][M_c:]]
+    nrm = np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    dist = np.einsum("ij,ij->i", g["pos"][M_c:] - V[T[:, 0]], nrm)
+    assert np.abs(dist).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# gather (Eq. 1 indirect part): closed form of one VPL over a plane, energy
+# ---------------------------------------------------------------------------
+def test_gather_single_vpl_closed_form(orc):
+    sc = plane_scene(half=100.0, albedo=0.5)
+    o = orc.OracleScene(sc)
+    h, Phi = 0.7, 3.0
+    s = np.linspace(0.0, 5.0, 41)
+    y = np.stack([s, np.zeros_like(s), np.zeros_like(s)], axis=1)
+    gb = dict(pos=y, nrm=np.tile([0, 0, 1.0], (len(s), 1)), rho=np.full((len(s), 3), 0.5),
+              tri=np.zeros(len(s), np.int64))
+    vpl = dict(pos=np.array([[0, 0, h]]), nrm=np.array([[0, 0, -1.0]]),
+               flux=np.array([[Phi, Phi, Phi]]))
+    out = o.gather(gb, vpl, d2_min=1e-8, eps=1e-6, vis_mode=1)
+    want = 0.5 * Phi * h * h / (math.pi ** 2 * (h * h + s * s) ** 2)
+    assert np.allclose(out[:, 0], want, rtol=1e-12)
+
+
+def test_gather_energy_conservation(orc):
+    """Irradiance E = pi L / rho of one VPL integrated over the receiving plane
+    equals its power (radial quadrature)."""
+    sc = plane_scene(half=1e4, albedo=1.0)
+    o = orc.OracleScene(sc)
+    h, Phi = 1.0, 1.0
+    # substitution s = h tan(a) maps [0, inf) to [0, pi/2)
+    a = (np.arange(20000) + 0.5) * (math.pi / 2) / 20000
+    s = h * np.tan(a)
+    y = np.stack([s, np.zeros_like(s), np.zeros_like(s)], axis=1)
+    gb = dict(pos=y, nrm=np.tile([0, 0, 1.0], (len(s), 1)), rho=np.ones((len(s), 3)),
+              tri=np.zeros(len(s), np.int64))
+    vpl = dict(pos=np.array([[0, 0, h]]), nrm=np.array([[0, 0, -1.0]]), flux=np.ones((1, 3)))
+    L = o.gather(gb, vpl, d2_min=1e-12, eps=1e-9, vis_mode=2)[:, 0]
+    E = math.pi * L
+    ds_da = h / np.cos(a) ** 2
+    total = (2 * math.pi * s * E * ds_da).sum() * (math.pi / 2) / 20000
+    assert abs(total - Phi) < 1e-6
+
+
+def test_gather_clamp_and_backfaces(orc):
+    sc = plane_scene(half=10.0, albedo=1.0)
+    o = orc.OracleScene(sc)
+    y = np.zeros((1, 3))
+    gb = dict(pos=y, nrm=np.array([[0, 0, 1.0]]), rho=np.ones((1, 3)), tri=np.zeros(1, np.int64))
+    # VPL facing away from the receiver contributes nothing
+    v1 = dict(pos=np.array([[0, 0, 1.0]]), nrm=np.array([[0, 0, 1.0]]), flux=np.ones((1, 3)))
+    assert o.gather(gb, v1, 1e-6, 1e-6, vis_mode=1)[0, 0] == 0.0
+    # below the clamp distance: cos cos / (pi d2_min)
+    h = 0.01
+    v2 = dict(pos=np.array([[0, 0, h]]), nrm=np.array([[0, 0, -1.0]]), flux=np.ones((1, 3)))
+    d2min = 0.04
+    out = o.gather(gb, v2, d2min, 1e-6, vis_mode=1)[0, 0]
+    assert abs(out - 1.0 / (math.pi ** 2 * float(F32(d2min)))) < 1e-9
+    # empty pixel stays black
+    gb_empty = dict(gb, tri=np.full(1, -1, np.int64))
+    assert o.gather(gb_empty, v2, d2min, 1e-6, vis_mode=1)[0, 0] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# visibility V (Eq. 1): a hand-built occluder, and BVH == brute force
+# ---------------------------------------------------------------------------
+def test_visibility_hand_occluder(orc):
+    sc = plane_scene(half=0.5, z=0.5)
+    o = orc.OracleScene(sc)
+    p = np.array([[0, 0, 0], [0, 0, 0], [0.9, 0, 0], [0, 0, 0], [0.2, 0.1, 1.0]], float)
+    q = np.array([[0, 0, 1], [0, 0, 0.49], [0.9, 0, 1], [0, 0, 0.5], [0.2, 0.1, 0.0]], float)
+    for vm in (0, 1):
+        assert o.occluded(p, q, vis_mode=vm).tolist() == [True, False, False, False, True]
+
+
+def _random_soup(n, seed):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0, 10, size=(n, 1, 3))
+    v = (c + rng.normal(0, 0.6, size=(n, 3, 3))).reshape(-1, 3)
+    return tri_scene(v, np.arange(3 * n).reshape(-1, 3), 0.5)
+
+
+@pytest.mark.parametrize("make", ["soup", "cornell", "room"])
+def test_bvh_equals_brute_force(orc, make):
+    if make == "soup":
+        sc = _random_soup(3000, 1)
+    elif make == "cornell":
+        sc = W.cornell_scene(0)
+    else:
+        s = W._Soup()
+        W._room_zup(s, (4.0, 4.0, 2.0), 4, 4, 2, albedo_fn=lambda: (0.5,) * 3)
+        rng = np.random.default_rng(3)
+        for _ in range(150):
+            lo = rng.uniform(0, 3.5, 3) * [1, 1, 0.3]
+            s.box(lo, lo + rng.uniform(0.1, 0.6, 3), (0.5, 0.5, 0.5))
+        sc = s.finish(W.cornell_scene(0).light)
+    o = orc.OracleScene(sc)
+    rng = np.random.default_rng(5)
+    lo, hi = sc.verts.min(0), sc.verts.max(0)
+    n = 3000
+    p = rng.uniform(lo, hi, size=(n, 3))
+    q = rng.uniform(lo, hi, size=(n, 3))
+    # axis-aligned and vertex-grazing rays too
+    q[: n // 4] = p[: n // 4] + np.eye(3)[rng.integers(0, 3, n // 4)] * 3.0
+    q[n // 4: n // 2] = sc.verts[rng.integers(0, len(sc.verts), n // 4)]
+    assert np.array_equal(o.occluded(p, q, 0), o.occluded(p, q, 1))
+    t0, tt0 = o.closest(p, q - p, 0.0, 0)
+    t1, tt1 = o.closest(p, q - p, 0.0, 1)
+    assert np.array_equal(t0, t1)
+    assert np.array_equal(tt0[t0 >= 0], tt1[t1 >= 0])
+
+
+def test_segment_margin(orc):
+    sc = plane_scene(half=0.5, z=0.5)
+    o = orc.OracleScene(sc)
+    # through the middle of a triangle: margin is the in-plane edge distance
+    m = o.segment_margin([0.2, -0.1, 0], [0.2, -0.1, 1])
+    assert 0.05 < m < 0.5
+    # passing 1e-7 outside the square's edge
+    m2 = o.segment_margin([0.5 + 1e-7, 0.1, 0], [0.5 + 1e-7, 0.1, 1])
+    assert m2 < 2e-7
+    # ending 1e-8 above the plane over the square
+    m3 = o.segment_margin([0.2, 0.1, 0], [0.2, 0.1, 0.5 - 1e-8])
+    assert m3 < 2e-8
+
+
+# ---------------------------------------------------------------------------
+# G-buffer: ray / plane intersection in closed form
+# ---------------------------------------------------------------------------
+def test_gbuffer_plane_closed_form(orc):
+    z = 2.0
+    sc = plane_scene(half=50.0, z=z, up=False)      # faces -z, towards the camera
+    o = orc.OracleScene(sc)
+    cam = _cam(eye=(0, 0, 0), fwd=(0, 0, 1), up=(0, 1, 0), w=16, h=8, vfov=50.0)
+    gb = o.gbuffer(cam)
+    tv = math.tan(math.radians(50.0) / 2)
+    th = tv * 16 / 8
+    for j in range(8):
+        for i in range(16):
+            k = j * 16 + i
+            sx = 2 * (i + 0.5) / 16 - 1
+            sy = 1 - 2 * (j + 0.5) / 8
+            # camera right = f x up = (0,0,1)x(0,1,0) = (-1,0,0)
+            want = np.array([-sx * th * z, sy * tv * z, z])
+            assert np.allclose(gb["pos"][k], want, rtol=0, atol=1e-12)
+            assert gb["tri"][k] in (0, 1)
+            assert np.allclose(gb["nrm"][k], [0, 0, -1])
+    # the same plane seen from behind leaves every pixel empty
+    o2 = orc.OracleScene(plane_scene(half=50.0, z=z, up=True))
+    assert (o2.gbuffer(cam)["tri"] == -1).all()
+
+
+# ---------------------------------------------------------------------------
+# whole pipeline on the tiny scene: budget split and counts
+# ---------------------------------------------------------------------------
+def test_pipeline_counts_tiny(orc):
+    wl = W.cornell_workload(width=32, height=32)
+    v = wl.views[0]
+    o = orc.OracleScene(wl.scene)
+    r = orc.render(o, v)
+    g = r["vpl"]
+    assert g["status"] == 0
+    assert len(g["pos"]) == 256 and g["n_close"] == 8 and g["m_far_kept"] == 64
+    assert (g["tag"][:192] == np.arange(192)).all()
+    assert np.isfinite(r["image"]).all() and (r["image"] >= 0).all()
+    assert r["image"].max() > 0
+    # brute-force and BVH visibility give the same image on the tiny scene
+    r0 = orc.render(o, v, vis_mode=0)
+    assert np.array_equal(r0["image"], r["image"])
