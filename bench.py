@@ -1,0 +1,377 @@
+"""Benchmark of the hybrid close-range VPL renderer on GB300.
+
+One step = one pass of the whole hot path over one synthetic view: scene upload
++ BVH build, G-buffer, VPL generation (close-range patch VPLs + sparse
+instant radiosity) and the per-pixel gather with BVH shadow rays, through the
+C ABI (vpl_scene_upload + vpl_render).  Workload: the procedural 200k-triangle
+room, 1024 x 1024 pixels, 4096 VPLs (3072 patch / 1024 instant radiosity).
+
+Metric: pixel-VPL contributions per second with visibility, i.e.
+width * height * VPLs per step / step time, summed over ranks (each rank
+renders its own view: replicas, weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pixel-VPL contributions/s with visibility"
+UNIT = "pairs/s"
+
+# executed FP32 operations per unit of gather work, counted from the source of
+# gather_kernel / warp_occluded / tri_hit (an FMA counts 2)
+FLOPS_PER_PAIR = 28       # d, |d|^2, two cosines, clamp, geometry factor, RGB FMA
+FLOPS_PER_RAY = 15        # segment end points and reciprocal direction
+FLOPS_PER_NODE = 40       # two slab tests per visited node (per active lane)
+FLOPS_PER_TRI = 47        # Moller-Trumbore (per active lane)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(workload, seconds: float = 12.0) -> dict:
+    """The FP64 oracle on a bounded sample of the same view: G-buffer of the
+    sampled pixels, full VPL generation, gather of the sampled pixels against
+    all VPLs.  Pairs/s on all host cores."""
+    import oracle
+    view = workload.views[0]
+    cam = view.camera
+    osc = oracle.OracleScene(workload.scene)
+    M = view.gen.m_close + view.gen.m_far
+    rng = np.random.default_rng(77)
+    n = 32
+    t_used = 0.0
+    pairs = 0
+    runs = 0
+    while True:
+        pix = rng.choice(cam.width * cam.height, n, replace=False)
+        t0 = time.perf_counter()
+        oracle.render(osc, view, pix)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        pairs += n * M
+        runs += 1
+        if t_used >= seconds or runs >= 50:
+            break
+        # grow the sample towards the time budget
+        n = int(min(4096, max(n, n * 0.5 * (seconds - t_used) / max(dt, 1e-3))))
+    return {"value": pairs / t_used, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{runs} oracle renders (FP64, own BVH) of {pairs // M} sampled pixels x {M} VPLs "
+                      f"incl. G-buffer of those pixels and full VPL generation, {t_used:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, steps of a
+    bounded sample of the same workload."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2203_11484_gb300 import workloads as W
+    oracle.build()
+    wl = W.room200k_workload()
+    view = wl.views[0]
+    cam = view.camera
+    osc = oracle.OracleScene(wl.scene)
+    M = view.gen.m_close + view.gen.m_far
+    n_pix = 64
+    rng = np.random.default_rng(5)
+    for _ in range(args.warmup):
+        oracle.render(osc, view, rng.choice(cam.width * cam.height, 8, replace=False))
+    times = []
+    for _ in range(args.steps):
+        pix = rng.choice(cam.width * cam.height, n_pix, replace=False)
+        t0 = time.perf_counter()
+        oracle.render(osc, view, pix)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n_pix * M * args.steps / total
+    sample = f"per step: {n_pix} sampled pixels x {M} VPLs, G-buffer of those pixels + full generation"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "width": cam.width, "height": cam.height,
+                                            "vpls": M, "tris": wl.scene.n_tris, "sample_pixels": n_pix},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2203_11484_gb300 import build as B
+    from paper_2203_11484_gb300 import vpl as V
+    from paper_2203_11484_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    B.build_library()
+
+    wl = W.room200k_workload(seed=1 + rank)  # each rank renders its own close-up view
+    view = wl.views[0]
+    cam, gen, gat = view.camera, view.gen, view.gather
+    M = gen.m_close + gen.m_far
+    npx = cam.width * cam.height
+    units = npx * M
+    sc = wl.scene
+    verts = torch.as_tensor(sc.verts).cuda()
+    tris = torch.as_tensor(sc.tris).cuda()
+    alb = torch.as_tensor(sc.albedo).cuda()
+    out = torch.zeros((npx, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    ctx = V.Context(dev)
+    gb = V.GBuffer.empty(cam.width, cam.height)
+    vs = V.VplSet.empty(M)
+
+    def step(o, gev=None):
+        """Whole hot path through the C ABI: upload + BVH, G-buffer, VPLs, gather."""
+        sid = V.vpl_scene_upload(ctx.h, verts, tris, alb, sc.light, stream)
+        V.vpl_gbuffer_build(ctx.h, sid, cam, gb, stream)
+        V.vpl_generate(ctx.h, sid, cam, gen, vs, stream)
+        if gev:
+            gev[0].record(stream)
+        V.vpl_gather(ctx.h, sid, gb, vs, gat, o, stream)
+        if gev:
+            gev[1].record(stream)
+        return sid
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- warm-up -------------------------------------------------------
+    sids = []
+    for _ in range(args.warmup):
+        sids.append(step(out))
+    rc = V.vpl_sync(ctx.h, stream, check=False)
+    if rc != 0:
+        raise RuntimeError(f"device status {rc}: {V.vpl_last_error(ctx.h)}")
+    for s in sids:
+        V.vpl_scene_release(ctx.h, s)
+
+    # ---- timed region: K steps, L2 flushed between steps ----------------
+    mk = lambda: torch.cuda.Event(enable_timing=True)
+    ev = [(mk(), mk()) for _ in range(args.steps)]
+    gev = [(mk(), mk()) for _ in range(args.steps)]
+    sids = []
+    clocks = ClockSampler(dev)
+    launches0 = V.vpl_launch_count(ctx.h)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        sids.append(step(out, gev[k]))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier()
+    clk = clocks.stop()
+    launches = V.vpl_launch_count(ctx.h) - launches0
+    rc = V.vpl_sync(ctx.h, stream, check=False)
+    if rc != 0:
+        raise RuntimeError(f"device status {rc}: {V.vpl_last_error(ctx.h)}")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    gather_ms = [a.elapsed_time(b) for a, b in gev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    for s in sids:
+        V.vpl_scene_release(ctx.h, s)
+    value = units * args.steps * ws / (total_ms / 1e3)
+
+    # ---- gather roofline: work counters of the last step's inputs (untimed) --
+    sid = V.vpl_scene_upload(ctx.h, verts, tris, alb, sc.light, stream)
+    V.vpl_gbuffer_build(ctx.h, sid, cam, gb, stream)
+    V.vpl_generate(ctx.h, sid, cam, gen, vs, stream)
+    cnt = V.vpl_gather_counters(ctx.h, sid, gb, vs, gat, stream)
+    V.vpl_sync(ctx.h, stream)
+    flops = (cnt[0] * FLOPS_PER_PAIR + cnt[1] * FLOPS_PER_RAY + cnt[2] * FLOPS_PER_NODE
+             + cnt[3] * FLOPS_PER_TRI)
+    gather_in_step_ms = statistics.mean(gather_ms)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = (clk.get("sm_max_mhz") or _peaks().get("sm_max_mhz") or 2070.0)
+    peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    achieved = flops / (gather_in_step_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "gather_kernel<BVH,FP32>",
+                "peak_note": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz",
+                "counters": {"pairs": cnt[0], "shadow_rays": cnt[1], "node_visits": cnt[2],
+                             "tri_tests": cnt[3], "blocked": cnt[4]},
+                "gather_ms": gather_in_step_ms,
+                "flops_per_unit": {"pair": FLOPS_PER_PAIR, "ray": FLOPS_PER_RAY, "node": FLOPS_PER_NODE,
+                                   "tri": FLOPS_PER_TRI}}
+    V.vpl_scene_release(ctx.h, sid)
+
+    # ---- end to end: host buffers in, image out, through the same API -----
+    e2e = None
+    if not args.no_e2e:
+        hv = torch.as_tensor(sc.verts).pin_memory()
+        ht = torch.as_tensor(sc.tris).pin_memory()
+        ha = torch.as_tensor(sc.albedo).pin_memory()
+        hout = torch.empty((npx, 4), dtype=torch.float32).pin_memory()
+        e_ms = []
+        sids = []
+        for k in range(max(1, min(args.steps, 5))):
+            flush.fill_(2.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s = V.vpl_scene_upload(ctx.h, hv, ht, ha, sc.light, stream)
+            V.vpl_render(ctx.h, s, cam, gen, gat, out, stream)
+            hout.copy_(out, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e_ms.append(e0.elapsed_time(e1))
+            sids.append(s)
+        V.vpl_sync(ctx.h, stream)
+        for s in sids:
+            V.vpl_scene_release(ctx.h, s)
+        h2d = hv.numel() * 4 + ht.numel() * 4 + ha.numel() * 4
+        e2e = {"value": units * ws / (statistics.mean(e_ms) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": hout.numel() * 4,
+               "ms_per_step": statistics.mean(e_ms)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(wl, seconds=args.cpu_seconds)
+        except Exception as exc:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "width": cam.width, "height": cam.height, "vpls": M,
+                           "m_close": gen.m_close, "m_far": gen.m_far, "tris": sc.n_tris,
+                           "visibility": "bvh", "parallelism": f"replicas x{ws}",
+                           "l2": "flushed (256 MB write) before every step; per-step CUDA events",
+                           "step": "scene upload + BVH build + G-buffer + VPL generation + gather"},
+                "views_per_s": ws * args.steps / (total_ms / 1e3),
+                "gather_ms_per_step": gather_in_step_ms,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk, "wall_s": wall}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,534 @@
+// Scene upload kernels: per-triangle preparation, device prefix sums, a
+// stable LSD radix sort and the linear BVH (Karras 2012 hierarchy over
+// 63-bit Morton codes, bounding boxes fitted bottom-up).  The BVH is not part
+// of the paper; it is the acceleration structure behind every ray query of
+// the method (G-buffer, light paths, Eq. 2 and Eq. 1 visibility).
+#include "vpl_internal.h"
+
+namespace vpl {
+
+// ==========================================================================
+// exclusive prefix sum (reduce / scan partials / scan tiles)
+// ==========================================================================
+constexpr int kScanThreads = 256, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive(T v, T *warp_tot, T &block_total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T n = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += n;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < kScanThreads / 32 ? warp_tot[lane] : T(0);
+        T ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T n = __shfl_up_sync(kFull, ti, o);
+            if (lane >= o) ti += n;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = ti - t; // exclusive warp offsets
+        if (lane == kScanThreads / 32 - 1) warp_tot[kScanThreads / 32] = ti;
+    }
+    __syncthreads();
+    T r = warp_tot[w] + inc - v;
+    block_total = warp_tot[kScanThreads / 32];
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const T *in, const int *n_dev, int64_t n_max, T *partial)
+{
+    __shared__ T wt[kScanThreads / 32 + 1];
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    T s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + (int64_t)threadIdx.x * kScanItems + k;
+        if (i < n) s += in[i];
+    }
+    T tot;
+    block_exclusive<T>(s, wt, tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(T *partial, int64_t n_tiles)
+{
+    __shared__ T wt[kScanThreads / 32 + 1];
+    T carry = 0;
+    for (int64_t b = 0; b < n_tiles; b += kScanThreads) {
+        int64_t i = b + threadIdx.x;
+        T v = i < n_tiles ? partial[i] : T(0);
+        T tot;
+        T ex = block_exclusive<T>(v, wt, tot);
+        if (i < n_tiles) partial[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const T *in, T *out, const int *n_dev, int64_t n_max, const T *partial)
+{
+    __shared__ T wt[kScanThreads / 32 + 1];
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (base > n) return;
+    T v[kScanItems];
+    T s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + (int64_t)threadIdx.x * kScanItems + k;
+        v[k] = i < n ? in[i] : T(0);
+        s += v[k];
+    }
+    T tot;
+    T run = block_exclusive<T>(s, wt, tot) + partial[blockIdx.x];
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + (int64_t)threadIdx.x * kScanItems + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    // the tile holding position n writes the total
+    if (threadIdx.x == 0 && n >= base && n < base + kScanTile) out[n] = partial[blockIdx.x] + tot;
+}
+
+template <typename T>
+cudaError_t exclusive_scan(const Exec &ex, const T *in, T *out, const int *n_dev, int64_t n_max)
+{
+    int64_t tiles = n_max / kScanTile + 1; // +1: position n_max needs a tile too
+    Tmp part;
+    VPL_TRY(part.alloc(ex, sizeof(T) * tiles));
+    scan_reduce_kernel<T><<<(unsigned)tiles, kScanThreads, 0, ex.stream>>>(in, n_dev, n_max, part.as<T>());
+    VPL_LAUNCHED(ex);
+    scan_partials_kernel<T><<<1, kScanThreads, 0, ex.stream>>>(part.as<T>(), tiles);
+    VPL_LAUNCHED(ex);
+    scan_down_kernel<T><<<(unsigned)tiles, kScanThreads, 0, ex.stream>>>(in, out, n_dev, n_max, part.as<T>());
+    VPL_LAUNCHED(ex);
+    return cudaSuccess;
+}
+
+template cudaError_t exclusive_scan<uint32_t>(const Exec &, const uint32_t *, uint32_t *, const int *, int64_t);
+template cudaError_t exclusive_scan<unsigned long long>(const Exec &, const unsigned long long *, unsigned long long *,
+                                                        const int *, int64_t);
+
+// ==========================================================================
+// stable LSD radix sort, 8 bits per pass
+// ==========================================================================
+constexpr int kSortThreads = 256, kSortItems = 4, kSortTile = kSortThreads * kSortItems;
+
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t *keys, const int *n_dev, int64_t n_max, int shift,
+                                  uint32_t *tile_hist, int n_tiles)
+{
+    __shared__ uint32_t h[256];
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; r++) {
+        int64_t i = base + r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    tile_hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout,
+                                     const int *n_dev, int64_t n_max, int shift,
+                                     const uint32_t *tile_off, int n_tiles)
+{
+    __shared__ uint32_t wc[kSortThreads / 32][256];
+    __shared__ uint32_t run[256];
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    if (base >= n) return;
+    run[threadIdx.x] = tile_off[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+    for (int r = 0; r < kSortItems; r++) {
+        int64_t i = base + r * kSortThreads + threadIdx.x;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0;
+        uint32_t val = valid ? vin[i] : 0;
+        uint32_t digit = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
+#pragma unroll
+        for (int q = 0; q < kSortThreads / 32; q++) wc[q][threadIdx.x] = 0;
+        __syncthreads();
+        unsigned peers = __match_any_sync(kFull, digit);
+        unsigned lower = peers & ((1u << lane) - 1u);
+        uint32_t rank = __popc(lower);
+        if (valid && lower == 0) wc[w][digit] = __popc(peers);
+        __syncthreads();
+        uint32_t acc = 0;
+#pragma unroll
+        for (int q = 0; q < kSortThreads / 32; q++) {
+            uint32_t c = wc[q][threadIdx.x];
+            wc[q][threadIdx.x] = acc;
+            acc += c;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t dst = run[digit] + wc[w][digit] + rank;
+            kout[dst] = key;
+            vout[dst] = val;
+        }
+        __syncthreads();
+        run[threadIdx.x] += acc;
+        __syncthreads();
+    }
+}
+
+cudaError_t radix_sort_pairs(const Exec &ex, uint64_t *keys, uint32_t *vals, const int *n_dev, int64_t n_max)
+{
+    if (n_max <= 0) return cudaSuccess;
+    const int n_tiles = (int)((n_max + kSortTile - 1) / kSortTile);
+    Tmp k2, v2, hist, off;
+    VPL_TRY(k2.alloc(ex, sizeof(uint64_t) * n_max));
+    VPL_TRY(v2.alloc(ex, sizeof(uint32_t) * n_max));
+    VPL_TRY(hist.alloc(ex, sizeof(uint32_t) * 256 * n_tiles));
+    VPL_TRY(off.alloc(ex, sizeof(uint32_t) * (256 * (int64_t)n_tiles + 1)));
+    uint64_t *ka = keys, *kb = k2.as<uint64_t>();
+    uint32_t *va = vals, *vb = v2.as<uint32_t>();
+    for (int shift = 0; shift < 64; shift += 8) {
+        radix_hist_kernel<<<n_tiles, kSortThreads, 0, ex.stream>>>(ka, n_dev, n_max, shift, hist.as<uint32_t>(), n_tiles);
+        VPL_LAUNCHED(ex);
+        VPL_TRY(exclusive_scan<uint32_t>(ex, hist.as<uint32_t>(), off.as<uint32_t>(), nullptr, 256 * (int64_t)n_tiles));
+        radix_scatter_kernel<<<n_tiles, kSortThreads, 0, ex.stream>>>(ka, va, kb, vb, n_dev, n_max, shift,
+                                                                      off.as<uint32_t>(), n_tiles);
+        VPL_LAUNCHED(ex);
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    // eight passes: the result is back in keys / vals
+    return cudaSuccess;
+}
+
+// ==========================================================================
+// scene preparation
+// ==========================================================================
+// order-preserving integer images of doubles / floats for atomic min / max
+__device__ __forceinline__ unsigned long long dkey(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double dunkey(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffULL) : ~k));
+}
+__device__ __forceinline__ unsigned fkey(float v)
+{
+    unsigned b = __float_as_uint(v);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float funkey(unsigned k) { return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k); }
+
+struct BoxKeys {
+    unsigned long long glo[3], ghi[3];
+    unsigned vlo[3], vhi[3];
+};
+
+__global__ void init_box_keys_kernel(BoxKeys *bk)
+{
+    for (int a = 0; a < 3; a++) {
+        bk->glo[a] = ~0ULL;
+        bk->ghi[a] = 0ULL;
+        bk->vlo[a] = ~0u;
+        bk->vhi[a] = 0u;
+    }
+}
+
+// vertex indices out of range are reported and replaced by 0 in the
+// library's copy, so that no later kernel reads outside the vertex array
+__global__ void validate_kernel(int32_t *tris, int64_t n_tris, int64_t n_verts, int *status)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tris) return;
+    for (int k = 0; k < 3; k++) {
+        int32_t v = tris[3 * t + k];
+        if (v < 0 || v >= n_verts) {
+            latch(status, VPL_ERR_INVALID_ARG);
+            tris[3 * t + k] = 0;
+        }
+    }
+}
+
+__global__ void prep_kernel(const float *verts, const int32_t *tris, const float *albedo, int64_t n_tris,
+                            int64_t n_verts, float4 *nrm, float4 *rho, BoxKeys *bk)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tris) return;
+    int32_t i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+    if (i0 < 0 || i0 >= n_verts || i1 < 0 || i1 >= n_verts || i2 < 0 || i2 >= n_verts) {
+        nrm[t] = make_float4(0, 0, 0, 0);
+        rho[t] = make_float4(0, 0, 0, 0);
+        return;
+    }
+    D3 a = dvert(verts, i0), b = dvert(verts, i1), c = dvert(verts, i2);
+    D3 cr = dcross(dsub(b, a), dsub(c, a));
+    double l = __dsqrt_rn(ddot(cr, cr));
+    D3 n = l > 0.0 ? dmk(__ddiv_rn(cr.x, l), __ddiv_rn(cr.y, l), __ddiv_rn(cr.z, l)) : dmk(0, 0, 0);
+    nrm[t] = make_float4((float)n.x, (float)n.y, (float)n.z, 0.0f);
+    rho[t] = make_float4(albedo[3 * t], albedo[3 * t + 1], albedo[3 * t + 2], 0.0f);
+    D3 s = dadd(dadd(a, b), c);
+    double g[3] = {__ddiv_rn(s.x, 3.0), __ddiv_rn(s.y, 3.0), __ddiv_rn(s.z, 3.0)};
+    for (int ax = 0; ax < 3; ax++) {
+        atomicMin(&bk->glo[ax], dkey(g[ax]));
+        atomicMax(&bk->ghi[ax], dkey(g[ax]));
+        float v0 = verts[3 * (int64_t)i0 + ax], v1 = verts[3 * (int64_t)i1 + ax], v2 = verts[3 * (int64_t)i2 + ax];
+        atomicMin(&bk->vlo[ax], fkey(fminf(v0, fminf(v1, v2))));
+        atomicMax(&bk->vhi[ax], fkey(fmaxf(v0, fmaxf(v1, v2))));
+    }
+}
+
+__global__ void finish_boxes_kernel(const BoxKeys *bk, double *gbox, float *vbox)
+{
+    for (int a = 0; a < 3; a++) {
+        gbox[a] = dunkey(bk->glo[a]);
+        gbox[3 + a] = dunkey(bk->ghi[a]);
+        vbox[a] = funkey(bk->vlo[a]);
+        vbox[3 + a] = funkey(bk->vhi[a]);
+    }
+}
+
+// 63-bit Morton code of the FP32 centroid in the vertex AABB
+__global__ void bvh_keys_kernel(const float *verts, const int32_t *tris, int64_t n_tris, const float *vbox,
+                                uint64_t *keys, uint32_t *vals)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tris) return;
+    uint32_t q[3];
+    for (int ax = 0; ax < 3; ax++) {
+        float c = (verts[3 * (int64_t)tris[3 * t] + ax] + verts[3 * (int64_t)tris[3 * t + 1] + ax] +
+                   verts[3 * (int64_t)tris[3 * t + 2] + ax]) * (1.0f / 3.0f);
+        float ext = vbox[3 + ax] - vbox[ax];
+        float u = ext > 0.0f ? (c - vbox[ax]) / ext : 0.0f;
+        float f = floorf(u * 2097152.0f);
+        q[ax] = (uint32_t)fminf(fmaxf(f, 0.0f), 2097151.0f);
+    }
+    keys[t] = morton63(q[0], q[1], q[2]);
+    vals[t] = (uint32_t)t;
+}
+
+// Karras (2012): one thread per internal node finds its key range and split
+__device__ __forceinline__ int delta(const uint64_t *k, int n, int i, int j)
+{
+    if (j < 0 || j >= n) return -1;
+    uint64_t a = k[i], b = k[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz(i ^ j);
+}
+
+__global__ void karras_kernel(const uint64_t *keys, int n, int *child, int *parent_int, int *parent_leaf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(keys, n, i, i - d);
+    int lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(keys, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gam = i + s * d + (d < 0 ? -1 : 0);
+    int lo = min(i, j), hi = max(i, j);
+    int c0 = (lo == gam) ? ~gam : gam;
+    int c1 = (hi == gam + 1) ? ~(gam + 1) : gam + 1;
+    child[2 * i] = c0;
+    child[2 * i + 1] = c1;
+    if (c0 < 0) parent_leaf[~c0] = i; else parent_int[c0] = i;
+    if (c1 < 0) parent_leaf[~c1] = i; else parent_int[c1] = i;
+    if (i == 0) parent_int[0] = -1;
+}
+
+// triangles in leaf order and their (padded) boxes
+__global__ void leaves_kernel(const float *verts, const int32_t *tris, const uint32_t *order, int64_t n_tris,
+                              const float *vbox, float4 *tri, float *leafbox)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_tris) return;
+    uint32_t t = order[k];
+    float3 v[3];
+    for (int q = 0; q < 3; q++) {
+        int64_t vi = tris[3 * (int64_t)t + q];
+        v[q] = make_float3(verts[3 * vi], verts[3 * vi + 1], verts[3 * vi + 2]);
+    }
+    tri[3 * k] = make_float4(v[0].x, v[0].y, v[0].z, __int_as_float((int)t));
+    float3 e1 = v[1] - v[0], e2 = v[2] - v[0];
+    tri[3 * k + 1] = make_float4(e1.x, e1.y, e1.z, 0.0f);
+    tri[3 * k + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+    // pad by a few ulps of the largest coordinate so that flat boxes of
+    // axis-aligned faces never lose a hit to rounding in the slab test
+    float m = 0.0f;
+    for (int a = 0; a < 6; a++) m = fmaxf(m, fabsf(vbox[a]));
+    float pad = m * 1e-6f + 1e-30f;
+    float *b = leafbox + 6 * k;
+    b[0] = fminf(v[0].x, fminf(v[1].x, v[2].x)) - pad;
+    b[1] = fminf(v[0].y, fminf(v[1].y, v[2].y)) - pad;
+    b[2] = fminf(v[0].z, fminf(v[1].z, v[2].z)) - pad;
+    b[3] = fmaxf(v[0].x, fmaxf(v[1].x, v[2].x)) + pad;
+    b[4] = fmaxf(v[0].y, fmaxf(v[1].y, v[2].y)) + pad;
+    b[5] = fmaxf(v[0].z, fmaxf(v[1].z, v[2].z)) + pad;
+}
+
+__device__ __forceinline__ void load_box(const float *p, float b[6])
+{
+    for (int a = 0; a < 6; a++) b[a] = __ldcg(p + a);
+}
+
+// bottom-up boxes: the second thread to reach a node merges its children
+__global__ void bounds_kernel(int n, const int *child, const int *parent_int, const int *parent_leaf,
+                              const float *leafbox, float *nodebox, int *visits, int *status)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int node = parent_leaf[k];
+    for (int steps = 0; node >= 0; steps++) {
+        if (steps > 4 * kStackMax) { // a well-formed hierarchy is never this deep
+            latch(status, VPL_ERR_TRAVERSAL_LIMIT);
+            return;
+        }
+        __threadfence();
+        if (atomicAdd(&visits[node], 1) == 0) return;
+        int c0 = child[2 * node], c1 = child[2 * node + 1];
+        float b0[6], b1[6];
+        load_box(c0 < 0 ? leafbox + 6 * (int64_t)(~c0) : nodebox + 6 * (int64_t)c0, b0);
+        load_box(c1 < 0 ? leafbox + 6 * (int64_t)(~c1) : nodebox + 6 * (int64_t)c1, b1);
+        float *o = nodebox + 6 * (int64_t)node;
+        for (int a = 0; a < 3; a++) {
+            __stcg(o + a, fminf(b0[a], b1[a]));
+            __stcg(o + 3 + a, fmaxf(b0[3 + a], b1[3 + a]));
+        }
+        node = parent_int[node];
+    }
+}
+
+__global__ void pack_nodes_kernel(int n, const int *child, const float *leafbox, const float *nodebox, float4 *nodes)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int c0 = child[2 * i], c1 = child[2 * i + 1];
+    const float *a = c0 < 0 ? leafbox + 6 * (int64_t)(~c0) : nodebox + 6 * (int64_t)c0;
+    const float *b = c1 < 0 ? leafbox + 6 * (int64_t)(~c1) : nodebox + 6 * (int64_t)c1;
+    float4 *o = nodes + 4 * (int64_t)i;
+    o[0] = make_float4(a[0], a[3], a[1], a[4]);
+    o[1] = make_float4(b[0], b[3], b[1], b[4]);
+    o[2] = make_float4(a[2], a[5], b[2], b[5]);
+    o[3] = make_float4(__int_as_float(c0), __int_as_float(c1), __int_as_float(1), __int_as_float(1));
+}
+
+// one triangle: a root whose first child is the leaf and whose second child
+// is an empty leaf far away
+__global__ void single_root_kernel(const float *leafbox, float4 *nodes)
+{
+    const float *a = leafbox;
+    const float far = 3.0e38f;
+    nodes[0] = make_float4(a[0], a[3], a[1], a[4]);
+    nodes[1] = make_float4(far, far, far, far);
+    nodes[2] = make_float4(a[2], a[5], far, far);
+    nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), __int_as_float(1), __int_as_float(0));
+}
+
+__global__ void depth_kernel(int n, const int *parent_int, const int *parent_leaf, int *depth, int *status)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int d = 0, node = n > 1 ? parent_leaf[k] : 0;
+    while (node >= 0 && d <= 4 * kStackMax) {
+        d++;
+        node = n > 1 ? parent_int[node] : -1;
+    }
+    atomicMax(depth, d);
+    if (d > kStackMax) latch(status, VPL_ERR_TRAVERSAL_LIMIT);
+}
+
+cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris,
+                        const float *albedo, SceneBuffers *sb)
+{
+    const int B = 256;
+    const int64_t T = n_tris;
+    const int n = (int)T;
+    sb->n_tris = T;
+    sb->n_verts = n_verts;
+    size_t bytes = 0;
+    auto dalloc = [&](void **p, size_t sz) -> cudaError_t {
+        bytes += sz;
+        return cudaMalloc(p, sz ? sz : 16);
+    };
+    VPL_TRY(dalloc((void **)&sb->verts, sizeof(float) * 3 * n_verts));
+    VPL_TRY(dalloc((void **)&sb->idx, sizeof(int32_t) * 3 * T));
+    VPL_TRY(dalloc((void **)&sb->tri, sizeof(float4) * 3 * T));
+    VPL_TRY(dalloc((void **)&sb->nodes, sizeof(float4) * 4 * (T > 1 ? T - 1 : 1)));
+    VPL_TRY(dalloc((void **)&sb->nrm, sizeof(float4) * T));
+    VPL_TRY(dalloc((void **)&sb->rho, sizeof(float4) * T));
+    VPL_TRY(dalloc((void **)&sb->gbox, sizeof(double) * 6));
+    VPL_TRY(dalloc((void **)&sb->vbox, sizeof(float) * 6));
+    VPL_TRY(dalloc((void **)&sb->depth, sizeof(int)));
+    sb->bytes = bytes;
+    VPL_TRY(cudaMemcpyAsync(sb->verts, verts, sizeof(float) * 3 * n_verts, cudaMemcpyDefault, ex.stream));
+    VPL_TRY(cudaMemcpyAsync(sb->idx, tris, sizeof(int32_t) * 3 * T, cudaMemcpyDefault, ex.stream));
+    Tmp alb, bk, keys, vals, leafbox, nodebox, child, pint, pleaf, visits;
+    VPL_TRY(alb.alloc(ex, sizeof(float) * 3 * T));
+    VPL_TRY(cudaMemcpyAsync(alb.p, albedo, sizeof(float) * 3 * T, cudaMemcpyDefault, ex.stream));
+    VPL_TRY(bk.alloc(ex, sizeof(BoxKeys)));
+    VPL_TRY(cudaMemsetAsync(sb->depth, 0, sizeof(int), ex.stream));
+
+    validate_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(sb->idx, T, n_verts, ex.status);
+    VPL_LAUNCHED(ex);
+    init_box_keys_kernel<<<1, 1, 0, ex.stream>>>(bk.as<BoxKeys>());
+    VPL_LAUNCHED(ex);
+    prep_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(sb->verts, sb->idx, alb.as<float>(), T, n_verts, sb->nrm,
+                                                     sb->rho, bk.as<BoxKeys>());
+    VPL_LAUNCHED(ex);
+    finish_boxes_kernel<<<1, 1, 0, ex.stream>>>(bk.as<BoxKeys>(), sb->gbox, sb->vbox);
+    VPL_LAUNCHED(ex);
+
+    VPL_TRY(keys.alloc(ex, sizeof(uint64_t) * T));
+    VPL_TRY(vals.alloc(ex, sizeof(uint32_t) * T));
+    bvh_keys_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(sb->verts, sb->idx, T, sb->vbox, keys.as<uint64_t>(),
+                                                         vals.as<uint32_t>());
+    VPL_LAUNCHED(ex);
+    VPL_TRY(radix_sort_pairs(ex, keys.as<uint64_t>(), vals.as<uint32_t>(), nullptr, T));
+
+    VPL_TRY(leafbox.alloc(ex, sizeof(float) * 6 * T));
+    leaves_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(sb->verts, sb->idx, vals.as<uint32_t>(), T, sb->vbox, sb->tri,
+                                                       leafbox.as<float>());
+    VPL_LAUNCHED(ex);
+    VPL_TRY(pleaf.alloc(ex, sizeof(int) * T));
+    VPL_TRY(pint.alloc(ex, sizeof(int) * (T > 1 ? T - 1 : 1)));
+    if (T == 1) {
+        single_root_kernel<<<1, 1, 0, ex.stream>>>(leafbox.as<float>(), sb->nodes);
+        VPL_LAUNCHED(ex);
+    } else {
+        VPL_TRY(nodebox.alloc(ex, sizeof(float) * 6 * (T - 1)));
+        VPL_TRY(child.alloc(ex, sizeof(int) * 2 * (T - 1)));
+        VPL_TRY(visits.alloc(ex, sizeof(int) * (T - 1)));
+        VPL_TRY(cudaMemsetAsync(visits.p, 0, sizeof(int) * (T - 1), ex.stream));
+        karras_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(keys.as<uint64_t>(), n, child.as<int>(), pint.as<int>(),
+                                                               pleaf.as<int>());
+        VPL_LAUNCHED(ex);
+        bounds_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(n, child.as<int>(), pint.as<int>(), pleaf.as<int>(),
+                                                           leafbox.as<float>(), nodebox.as<float>(), visits.as<int>(),
+                                                           ex.status);
+        VPL_LAUNCHED(ex);
+        pack_nodes_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, child.as<int>(), leafbox.as<float>(),
+                                                                   nodebox.as<float>(), sb->nodes);
+        VPL_LAUNCHED(ex);
+    }
+    depth_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(n, pint.as<int>(), pleaf.as<int>(), sb->depth, ex.status);
+    VPL_LAUNCHED(ex);
+    return cudaSuccess;
+}
+
+} // namespace vpl

@@ -1,0 +1,656 @@
+// The C ABI of libvpl (declared in include/vpl.h): contexts, the scene
+// registry, argument checks, the camera frame, and the order of launches of
+// each pipeline step.  Host code here is compiled with -ffp-contract=off: the
+// camera frame feeds the exact FP64 close-range decisions.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "vpl_internal.h"
+
+using namespace vpl;
+
+namespace {
+
+struct SceneRec {
+    SceneBuffers b;
+    vpl_light light;
+};
+
+void free_scene(SceneBuffers &b)
+{
+    void *ps[] = {b.tri, b.nodes, b.nrm, b.rho, b.verts, b.idx, b.gbox, b.vbox, b.depth};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    b = SceneBuffers();
+}
+
+} // namespace
+
+struct vpl_ctx {
+    int device = 0;
+    std::string err;
+    int *d_status = nullptr;
+    GenInfoDev *d_info = nullptr;
+    std::map<uint64_t, SceneRec *> scenes;
+    uint64_t next_id = 1;
+    int64_t launches = 0;
+    bool timing = false;
+    cudaEvent_t ev[6] = {};
+    bool ev_valid[6] = {};
+    cudaMemPool_t pool = nullptr;
+};
+
+namespace {
+
+const double kPiHost = 3.14159265358979323846;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(vpl_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(vpl_ctx *ctx, cudaError_t e, const char *where)
+{
+    cudaGetLastError(); // clear a sticky launch error so later calls are not confused
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? VPL_ERR_OOM : VPL_ERR_CUDA, m);
+}
+
+#define CK(ctx, expr, where)                                     \
+    do {                                                         \
+        cudaError_t e__ = (expr);                                \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, where); \
+    } while (0)
+
+Exec exec_of(vpl_ctx *ctx, vpl_stream stream)
+{
+    Exec e;
+    e.stream = (cudaStream_t)stream;
+    e.launches = &ctx->launches;
+    e.status = ctx->d_status;
+    e.pool = ctx->pool;
+    e.timing = ctx->timing;
+    return e;
+}
+
+void mark(vpl_ctx *ctx, int k, vpl_stream stream)
+{
+    if (!ctx->timing) return;
+    cudaEventRecord(ctx->ev[k], (cudaStream_t)stream);
+    ctx->ev_valid[k] = true;
+}
+
+bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int check_light(vpl_ctx *ctx, const vpl_light *L)
+{
+    if (!L) return fail(ctx, VPL_ERR_INVALID_ARG, "light is NULL");
+    if (L->type != VPL_LIGHT_AREA && L->type != VPL_LIGHT_POINT)
+        return fail(ctx, VPL_ERR_INVALID_ARG, "light.type must be 0 (area) or 1 (point)");
+    if (!finite3(L->center) || !finite3(L->normal) || !finite3(L->edge_u) || !finite3(L->edge_v) ||
+        !finite3(L->power))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "light fields must be finite");
+    for (int c = 0; c < 3; c++)
+        if (L->power[c] < 0.0f) return fail(ctx, VPL_ERR_INVALID_ARG, "light.power must be >= 0");
+    return VPL_OK;
+}
+
+struct Frame {
+    double e[3], f[3], r[3], u[3], tv, th;
+};
+
+double dot3(const double *a, const double *b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// camera frame: f = forward/|forward|, r = unit(f x up), u = r x f,
+// tan(vfov/2) and tan(hfov/2) = tan(vfov/2) W / H
+int camera_frame(vpl_ctx *ctx, const vpl_camera *c, Frame *F)
+{
+    if (!c) return fail(ctx, VPL_ERR_INVALID_ARG, "camera is NULL");
+    if (c->width < 0 || c->height < 0 || (int64_t)c->width * c->height > (int64_t)1 << 31)
+        return fail(ctx, VPL_ERR_INVALID_ARG, "camera width/height out of range");
+    if (!(c->vfov_deg > 0.0f && c->vfov_deg < 180.0f))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "camera vfov_deg must lie in (0, 180)");
+    if (!finite3(c->eye) || !finite3(c->forward) || !finite3(c->up))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "camera vectors must be finite");
+    double fw[3] = {(double)c->forward[0], (double)c->forward[1], (double)c->forward[2]};
+    double up[3] = {(double)c->up[0], (double)c->up[1], (double)c->up[2]};
+    double l = std::sqrt(dot3(fw, fw));
+    if (!(l > 0.0)) return fail(ctx, VPL_ERR_INVALID_ARG, "camera forward is zero");
+    for (int a = 0; a < 3; a++) {
+        F->e[a] = (double)c->eye[a];
+        F->f[a] = fw[a] / l;
+    }
+    double rr[3];
+    cross3(F->f, up, rr);
+    double lr = std::sqrt(dot3(rr, rr));
+    if (!(lr > 0.0)) return fail(ctx, VPL_ERR_INVALID_ARG, "camera up is parallel to forward");
+    for (int a = 0; a < 3; a++) F->r[a] = rr[a] / lr;
+    cross3(F->r, F->f, F->u);
+    F->tv = std::tan((double)c->vfov_deg * (kPiHost / 180.0) * 0.5);
+    F->th = c->height > 0 ? (F->tv * (double)c->width) / (double)c->height : F->tv;
+    return VPL_OK;
+}
+
+SceneRec *find_scene(vpl_ctx *ctx, vpl_scene_id id)
+{
+    auto it = ctx->scenes.find(id);
+    return it == ctx->scenes.end() ? nullptr : it->second;
+}
+
+SceneView view_of(const SceneRec *s)
+{
+    SceneView v;
+    v.n_tris = (int32_t)s->b.n_tris;
+    v.n_nodes = (int32_t)(s->b.n_tris > 1 ? s->b.n_tris - 1 : 1);
+    v.tri = s->b.tri;
+    v.nodes = s->b.nodes;
+    v.nrm = s->b.nrm;
+    v.rho = s->b.rho;
+    v.verts = s->b.verts;
+    v.idx = s->b.idx;
+    v.gbox = s->b.gbox;
+    return v;
+}
+
+LightView light_of(const vpl_light &L)
+{
+    LightView v;
+    memcpy(v.center, L.center, sizeof v.center);
+    memcpy(v.normal, L.normal, sizeof v.normal);
+    memcpy(v.edge_u, L.edge_u, sizeof v.edge_u);
+    memcpy(v.edge_v, L.edge_v, sizeof v.edge_v);
+    memcpy(v.power, L.power, sizeof v.power);
+    v.type = L.type;
+    return v;
+}
+
+int check_gbuffer(vpl_ctx *ctx, const vpl_gbuffer *g, const vpl_camera *cam)
+{
+    if (!g) return fail(ctx, VPL_ERR_INVALID_ARG, "gbuffer is NULL");
+    if (g->width < 0 || g->height < 0) return fail(ctx, VPL_ERR_INVALID_ARG, "gbuffer size negative");
+    if (cam && (g->width != cam->width || g->height != cam->height))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "gbuffer size differs from the camera's");
+    if (g->format != VPL_FORMAT_FP32 && g->format != VPL_FORMAT_FP16)
+        return fail(ctx, VPL_ERR_INVALID_ARG, "gbuffer format must be 0 (FP32) or 1 (FP16)");
+    if ((int64_t)g->width * g->height > 0 && (!g->pos || !g->nrm || !g->albedo))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "gbuffer pointers must be non-NULL");
+    return VPL_OK;
+}
+
+int check_vpls(vpl_ctx *ctx, const vpl_vpl_set *v)
+{
+    if (!v) return fail(ctx, VPL_ERR_INVALID_ARG, "vpl set is NULL");
+    if (v->count < 0) return fail(ctx, VPL_ERR_INVALID_ARG, "vpl count negative");
+    if (v->format != VPL_FORMAT_FP32 && v->format != VPL_FORMAT_FP16)
+        return fail(ctx, VPL_ERR_INVALID_ARG, "vpl format must be 0 (FP32) or 1 (FP16)");
+    if (v->count > 0 && (!v->pos || !v->nrm || !v->flux))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "vpl pointers must be non-NULL");
+    return VPL_OK;
+}
+
+int check_gather(vpl_ctx *ctx, const vpl_gather_params *p, int gfmt, int vfmt)
+{
+    if (!p) return fail(ctx, VPL_ERR_INVALID_ARG, "gather params are NULL");
+    if (p->visibility < 0 || p->visibility > 2) return fail(ctx, VPL_ERR_INVALID_ARG, "visibility must be 0, 1 or 2");
+    if (p->precision < 0 || p->precision > 2) return fail(ctx, VPL_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
+    if (!(p->d2_min >= 0.0f) || !std::isfinite(p->d2_min)) return fail(ctx, VPL_ERR_INVALID_ARG, "d2_min must be >= 0");
+    if (!(p->ray_eps >= 0.0f) || !std::isfinite(p->ray_eps)) return fail(ctx, VPL_ERR_INVALID_ARG, "ray_eps must be >= 0");
+    int want = p->precision == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
+    if (gfmt != want || vfmt != want)
+        return fail(ctx, VPL_ERR_INVALID_ARG, "buffer formats must be FP32 for precision 0 and FP16 otherwise");
+    if (p->precision != VPL_PREC_FP32)
+        return fail(ctx, VPL_ERR_UNSUPPORTED, "FP16-attribute gather is not built into this library");
+    return VPL_OK;
+}
+
+int check_gen(vpl_ctx *ctx, const vpl_gen_params *g)
+{
+    if (!g) return fail(ctx, VPL_ERR_INVALID_ARG, "gen params are NULL");
+    if (g->m_close < 0 || g->m_far < 0) return fail(ctx, VPL_ERR_INVALID_ARG, "m_close / m_far must be >= 0");
+    if (g->max_bounces < 1 || g->max_bounces > 15) return fail(ctx, VPL_ERR_INVALID_ARG, "max_bounces must be 1..15");
+    if (g->light_samples < 1) return fail(ctx, VPL_ERR_INVALID_ARG, "light_samples must be >= 1");
+    if (!(g->d_close >= 0.0) || !std::isfinite(g->d_close)) return fail(ctx, VPL_ERR_INVALID_ARG, "d_close must be >= 0");
+    if (!(g->ray_eps >= 0.0f) || !std::isfinite(g->ray_eps)) return fail(ctx, VPL_ERR_INVALID_ARG, "ray_eps must be >= 0");
+    if (g->ir_max_paths < 0 || g->ir_max_paths > ((int64_t)1 << 26))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "ir_max_paths must be in [0, 2^26]");
+    if ((int64_t)g->m_close + g->m_far > ((int64_t)1 << 30)) return fail(ctx, VPL_ERR_INVALID_ARG, "too many VPLs");
+    return VPL_OK;
+}
+
+GenArgs gen_args(const Frame &F, const vpl_gen_params *g, const vpl_light &L)
+{
+    GenArgs a;
+    a.d_close = g->d_close;
+    a.ray_eps = g->ray_eps;
+    a.m_close = g->m_close;
+    a.m_far = g->m_far;
+    a.max_bounces = g->max_bounces;
+    a.light_samples = g->light_samples;
+    a.max_paths = g->ir_max_paths > 0 ? g->ir_max_paths : 16 * (int64_t)g->m_far + 4096;
+    a.seed = g->seed;
+    for (int k = 0; k < 3; k++) {
+        a.eye[k] = F.e[k];
+        a.f[k] = F.f[k];
+        a.r[k] = F.r[k];
+        a.u[k] = F.u[k];
+    }
+    a.tv = F.tv;
+    a.th = F.th;
+    a.light = light_of(L);
+    return a;
+}
+
+CamArgs cam_args(const Frame &F, const vpl_camera *c)
+{
+    CamArgs a;
+    for (int k = 0; k < 3; k++) {
+        a.eye[k] = (float)F.e[k];
+        a.f[k] = (float)F.f[k];
+        a.r[k] = (float)F.r[k];
+        a.u[k] = (float)F.u[k];
+    }
+    a.tv = (float)F.tv;
+    a.th = (float)F.th;
+    a.width = c->width;
+    a.height = c->height;
+    return a;
+}
+
+GatherArgs gather_args(const vpl_gbuffer *g, const vpl_vpl_set *v, const vpl_gather_params *p, float *out)
+{
+    GatherArgs a;
+    a.width = g->width;
+    a.height = g->height;
+    a.count = v->count;
+    a.d2_min = p->d2_min;
+    a.ray_eps = p->ray_eps;
+    a.precision = p->precision;
+    a.visibility = p->visibility;
+    a.g_pos = (const float4 *)g->pos;
+    a.g_nrm = g->nrm;
+    a.g_alb = g->albedo;
+    a.v_pos = (const float4 *)v->pos;
+    a.v_nrm = v->nrm;
+    a.v_flux = v->flux;
+    a.out = (float4 *)out;
+    return a;
+}
+
+} // namespace
+
+extern "C" {
+
+int vpl_create(vpl_ctx **out, int device)
+{
+    if (!out) return VPL_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return device < 0 || (n > 0 && device >= n) ? VPL_ERR_INVALID_ARG : VPL_ERR_CUDA;
+    }
+    DeviceGuard g(device);
+    vpl_ctx *ctx = new vpl_ctx();
+    ctx->device = device;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_info, sizeof(GenInfoDev)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_info, 0, sizeof(GenInfoDev)) != cudaSuccess ||
+        cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        vpl_destroy(ctx);
+        return VPL_ERR_CUDA;
+    }
+    uint64_t keep = ~0ULL;
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    for (auto &e : ctx->ev) cudaEventCreate(&e);
+    *out = ctx;
+    return VPL_OK;
+}
+
+void vpl_destroy(vpl_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->scenes) {
+        free_scene(kv.second->b);
+        delete kv.second;
+    }
+    ctx->scenes.clear();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_info) cudaFree(ctx->d_info);
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    delete ctx;
+}
+
+const char *vpl_last_error(const vpl_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int vpl_scene_upload(vpl_ctx *ctx, const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris,
+                     const float *albedo, const vpl_light *light, vpl_stream stream, vpl_scene_id *out)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    if (!out) return fail(ctx, VPL_ERR_INVALID_ARG, "out is NULL");
+    *out = 0;
+    if (!verts || !tris || !albedo) return fail(ctx, VPL_ERR_INVALID_ARG, "scene arrays must be non-NULL");
+    if (n_tris < 1 || n_tris > ((int64_t)1 << 30)) return fail(ctx, VPL_ERR_INVALID_ARG, "n_tris must be in [1, 2^30]");
+    if (n_verts < 1 || n_verts > ((int64_t)1 << 31) - 1) return fail(ctx, VPL_ERR_INVALID_ARG, "n_verts out of range");
+    int rc = check_light(ctx, light);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    SceneRec *s = new SceneRec();
+    s->light = *light;
+    Exec ex = exec_of(ctx, stream);
+    mark(ctx, 0, stream);
+    cudaError_t e = build_scene(ex, verts, n_verts, tris, n_tris, albedo, &s->b);
+    mark(ctx, 1, stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        free_scene(s->b);
+        delete s;
+        return cuda_fail(ctx, e, "vpl_scene_upload");
+    }
+    uint64_t id = ctx->next_id++;
+    ctx->scenes[id] = s;
+    *out = id;
+    return VPL_OK;
+}
+
+int vpl_scene_release(vpl_ctx *ctx, vpl_scene_id scene)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize(); // work in flight may still read the scene
+    free_scene(s->b);
+    delete s;
+    ctx->scenes.erase(scene);
+    return VPL_OK;
+}
+
+int vpl_scene_query(vpl_ctx *ctx, vpl_scene_id scene, vpl_scene_info *out)
+{
+    if (!ctx || !out) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    DeviceGuard g(ctx->device);
+    CK(ctx, cudaDeviceSynchronize(), "vpl_scene_query");
+    int depth = 0;
+    float box[6];
+    CK(ctx, cudaMemcpy(&depth, s->b.depth, sizeof depth, cudaMemcpyDeviceToHost), "vpl_scene_query");
+    CK(ctx, cudaMemcpy(box, s->b.vbox, sizeof box, cudaMemcpyDeviceToHost), "vpl_scene_query");
+    out->n_tris = s->b.n_tris;
+    out->n_nodes = s->b.n_tris > 1 ? s->b.n_tris - 1 : 1;
+    out->depth = depth;
+    out->device_bytes = (int64_t)s->b.bytes;
+    memcpy(out->bounds_lo, box, sizeof out->bounds_lo);
+    memcpy(out->bounds_hi, box + 3, sizeof out->bounds_hi);
+    return VPL_OK;
+}
+
+int vpl_gbuffer_build(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const vpl_gbuffer *out,
+                      vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    Frame F;
+    int rc = camera_frame(ctx, cam, &F);
+    if (rc) return rc;
+    if ((rc = check_gbuffer(ctx, out, cam))) return rc;
+    DeviceGuard g(ctx->device);
+    Exec ex = exec_of(ctx, stream);
+    CK(ctx, gbuffer_build(ex, view_of(s), cam_args(F, cam), false, (float4 *)out->pos, out->nrm, out->albedo,
+                          out->format),
+       "vpl_gbuffer_build");
+    return VPL_OK;
+}
+
+int vpl_generate(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const vpl_gen_params *gen,
+                 const vpl_vpl_set *vpls, vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    Frame F;
+    int rc = camera_frame(ctx, cam, &F);
+    if (rc) return rc;
+    if ((rc = check_gen(ctx, gen))) return rc;
+    if ((rc = check_vpls(ctx, vpls))) return rc;
+    if (vpls->count != gen->m_close + gen->m_far)
+        return fail(ctx, VPL_ERR_INVALID_ARG, "vpl set count must equal m_close + m_far");
+    if (vpls->format != VPL_FORMAT_FP32)
+        return fail(ctx, VPL_ERR_UNSUPPORTED, "vpl_generate writes FP32 VPL sets");
+    DeviceGuard g(ctx->device);
+    Exec ex = exec_of(ctx, stream);
+    CK(ctx, generate_vpls(ex, view_of(s), gen_args(F, gen, s->light), (float4 *)vpls->pos, vpls->nrm, vpls->flux,
+                          vpls->format, ctx->d_info),
+       "vpl_generate");
+    return VPL_OK;
+}
+
+int vpl_generate_info(vpl_ctx *ctx, vpl_gen_info *out)
+{
+    if (!ctx || !out) return VPL_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    CK(ctx, cudaDeviceSynchronize(), "vpl_generate_info");
+    GenInfoDev d;
+    int st = 0;
+    CK(ctx, cudaMemcpy(&d, ctx->d_info, sizeof d, cudaMemcpyDeviceToHost), "vpl_generate_info");
+    CK(ctx, cudaMemcpy(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost), "vpl_generate_info");
+    out->n_close = d.n_close;
+    out->shift_s = d.shift_s;
+    out->f_total = d.f_total;
+    out->paths = d.paths;
+    out->m_far_kept = d.m_far_kept;
+    out->status = st;
+    return VPL_OK;
+}
+
+int vpl_gather(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf, const vpl_vpl_set *vpls,
+               const vpl_gather_params *params, float *out_rgba, vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    int rc = check_gbuffer(ctx, gbuf, nullptr);
+    if (rc) return rc;
+    if ((rc = check_vpls(ctx, vpls))) return rc;
+    if ((rc = check_gather(ctx, params, gbuf->format, vpls->format))) return rc;
+    if ((int64_t)gbuf->width * gbuf->height > 0 && !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "out_rgba is NULL");
+    DeviceGuard g(ctx->device);
+    Exec ex = exec_of(ctx, stream);
+    for (int k = 2; k < 4; k++) ctx->ev_valid[k] = false;
+    mark(ctx, 4, stream);
+    CK(ctx, gather(ex, view_of(s), gather_args(gbuf, vpls, params, out_rgba)), "vpl_gather");
+    mark(ctx, 5, stream);
+    return VPL_OK;
+}
+
+int vpl_render(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const vpl_gen_params *gen,
+               const vpl_gather_params *params, float *out_rgba, vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    Frame F;
+    int rc = camera_frame(ctx, cam, &F);
+    if (rc) return rc;
+    if ((rc = check_gen(ctx, gen))) return rc;
+    if ((rc = check_gather(ctx, params, VPL_FORMAT_FP32, VPL_FORMAT_FP32))) return rc;
+    const int64_t npx = (int64_t)cam->width * cam->height;
+    if (npx > 0 && !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "out_rgba is NULL");
+    DeviceGuard g(ctx->device);
+    Exec ex = exec_of(ctx, stream);
+    const int64_t M = (int64_t)gen->m_close + gen->m_far;
+    Tmp gpos, gnrm, galb, vpos, vnrm, vflux;
+    CK(ctx, gpos.alloc(ex, sizeof(float4) * npx), "vpl_render");
+    CK(ctx, gnrm.alloc(ex, sizeof(float4) * npx), "vpl_render");
+    CK(ctx, galb.alloc(ex, sizeof(float4) * npx), "vpl_render");
+    CK(ctx, vpos.alloc(ex, sizeof(float4) * M), "vpl_render");
+    CK(ctx, vnrm.alloc(ex, sizeof(float4) * M), "vpl_render");
+    CK(ctx, vflux.alloc(ex, sizeof(float4) * M), "vpl_render");
+    vpl_gbuffer gb = {gpos.p, gnrm.p, galb.p, cam->width, cam->height, VPL_FORMAT_FP32, 0};
+    vpl_vpl_set vs = {vpos.p, vnrm.p, vflux.p, (int32_t)M, VPL_FORMAT_FP32};
+    SceneView v = view_of(s);
+    mark(ctx, 2, stream);
+    CK(ctx, gbuffer_build(ex, v, cam_args(F, cam), params->visibility == VPL_VIS_BRUTE, gpos.as<float4>(), gnrm.p,
+                          galb.p, VPL_FORMAT_FP32),
+       "vpl_render gbuffer");
+    mark(ctx, 3, stream);
+    CK(ctx, generate_vpls(ex, v, gen_args(F, gen, s->light), vpos.as<float4>(), vnrm.p, vflux.p, VPL_FORMAT_FP32,
+                          ctx->d_info),
+       "vpl_render generate");
+    mark(ctx, 4, stream);
+    CK(ctx, gather(ex, v, gather_args(&gb, &vs, params, out_rgba)), "vpl_render gather");
+    mark(ctx, 5, stream);
+    return VPL_OK;
+}
+
+int vpl_sync(vpl_ctx *ctx, vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    CK(ctx, cudaStreamSynchronize((cudaStream_t)stream), "vpl_sync");
+    int st = 0;
+    CK(ctx, cudaMemcpy(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost), "vpl_sync");
+    if (st != 0) {
+        CK(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)), "vpl_sync");
+        const char *what = st == VPL_ERR_TRAVERSAL_LIMIT   ? "a BVH walk hit its step or stack limit"
+                           : st == VPL_ERR_EMPTY_CLOSE     ? "no close-range face for m_close > 0"
+                           : st == VPL_ERR_PATHS_EXHAUSTED ? "ir_max_paths light paths gave fewer than m_far VPLs"
+                           : st == VPL_ERR_INVALID_ARG     ? "a triangle index was out of range"
+                                                           : "device error";
+        ctx->err = what;
+    }
+    return st;
+}
+
+int vpl_debug_philox(vpl_ctx *ctx, const uint64_t *ctr, const uint64_t *key, int64_t n, uint64_t *out,
+                     vpl_stream stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(ctx, VPL_ERR_INVALID_ARG, "bad philox args");
+    DeviceGuard g(ctx->device);
+    CK(ctx, debug_philox(exec_of(ctx, stream), ctr, key, n, out), "vpl_debug_philox");
+    return VPL_OK;
+}
+
+int vpl_debug_rays(vpl_ctx *ctx, vpl_scene_id scene, int32_t mode, int32_t brute, const float *a, const float *b,
+                   int64_t n, int32_t *out_tri, float *out_t, vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    if ((mode != 0 && mode != 1) || n < 0 || (n > 0 && (!a || !b || !out_tri)))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "bad ray query args");
+    DeviceGuard g(ctx->device);
+    CK(ctx, debug_rays(exec_of(ctx, stream), view_of(s), mode, brute, (const float4 *)a, (const float4 *)b, n, out_tri,
+                       out_t),
+       "vpl_debug_rays");
+    return VPL_OK;
+}
+
+int vpl_debug_visibility(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf, const vpl_vpl_set *vpls,
+                         const vpl_gather_params *params, const int32_t *pixels, int64_t n_pixels, int8_t *vis,
+                         vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    int rc = check_gbuffer(ctx, gbuf, nullptr);
+    if (rc) return rc;
+    if ((rc = check_vpls(ctx, vpls))) return rc;
+    if ((rc = check_gather(ctx, params, gbuf->format, vpls->format))) return rc;
+    if (n_pixels < 0 || (n_pixels > 0 && (!pixels || !vis))) return fail(ctx, VPL_ERR_INVALID_ARG, "bad pixel list");
+    DeviceGuard g(ctx->device);
+    CK(ctx, gather_visibility(exec_of(ctx, stream), view_of(s), gather_args(gbuf, vpls, params, nullptr), pixels,
+                              n_pixels, vis),
+       "vpl_debug_visibility");
+    return VPL_OK;
+}
+
+int vpl_set_timing(vpl_ctx *ctx, int32_t on)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    ctx->timing = on != 0;
+    return VPL_OK;
+}
+
+int vpl_stage_times(vpl_ctx *ctx, float *ms, int32_t n)
+{
+    if (!ctx || (n > 0 && !ms)) return VPL_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    const int pairs[4][2] = {{0, 1}, {2, 3}, {3, 4}, {4, 5}};
+    for (int k = 0; k < n && k < 4; k++) {
+        ms[k] = -1.0f;
+        int a = pairs[k][0], b = pairs[k][1];
+        if (ctx->ev_valid[a] && ctx->ev_valid[b]) {
+            CK(ctx, cudaEventSynchronize(ctx->ev[b]), "vpl_stage_times");
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]) == cudaSuccess) ms[k] = t;
+            else cudaGetLastError();
+        }
+    }
+    return VPL_OK;
+}
+
+int64_t vpl_launch_count(const vpl_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int vpl_gather_counters(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf, const vpl_vpl_set *vpls,
+                        const vpl_gather_params *params, uint64_t out[5], vpl_stream stream)
+{
+    if (!ctx || !out) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    int rc = check_gbuffer(ctx, gbuf, nullptr);
+    if (rc) return rc;
+    if ((rc = check_vpls(ctx, vpls))) return rc;
+    if ((rc = check_gather(ctx, params, gbuf->format, vpls->format))) return rc;
+    DeviceGuard g(ctx->device);
+    Exec ex = exec_of(ctx, stream);
+    unsigned long long *d = nullptr;
+    CK(ctx, cudaMallocFromPoolAsync((void **)&d, sizeof(unsigned long long) * 5, ctx->pool, ex.stream),
+       "vpl_gather_counters");
+    cudaError_t e = gather_counters(ex, view_of(s), gather_args(gbuf, vpls, params, nullptr), d);
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, ex.stream);
+    cudaFreeAsync(d, ex.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ex.stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "vpl_gather_counters");
+    for (int k = 0; k < 5; k++) out[k] = h[k];
+    return VPL_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,313 @@
+// Primary-ray G-buffer and the per-pixel indirect gather (Eq. 1 indirect
+// term, Sec. 3 pipeline step (4)), plus the diagnostic kernels.
+//
+// Gather organisation: a warp owns an 8 x 4 pixel tile and walks the whole VPL
+// list in chunks of 32.  Each chunk is read with coalesced float4 loads into
+// a per-warp slice of shared memory and then broadcast VPL by VPL to all 32
+// lanes, so the 32 shadow segments of one step all end at the same VPL and
+// start from neighbouring pixels: the warp traverses the BVH as one packet
+// (warp_occluded).  Tiles are handed out dynamically (an atomic counter) to a
+// grid of resident blocks.  Each pixel sums its VPLs in index order in one
+// thread, so the result does not depend on tiling or batching.
+#include "vpl_internal.h"
+
+namespace vpl {
+
+constexpr int kGatherWarps = 4;
+constexpr int kTileW = 8, kTileH = 4;
+
+__device__ __forceinline__ float4 load_attr(const void *base, int64_t i, int fmt)
+{
+    if (fmt == VPL_FORMAT_FP16) {
+        const __half2 *p = reinterpret_cast<const __half2 *>(base) + 2 * i;
+        float2 a = __half22float2(p[0]), b = __half22float2(p[1]);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    return __ldg(reinterpret_cast<const float4 *>(base) + i);
+}
+
+__device__ __forceinline__ void store_attr_g(void *base, int64_t i, float4 v, int fmt)
+{
+    if (fmt == VPL_FORMAT_FP16) {
+        __half2 *p = reinterpret_cast<__half2 *>(base) + 2 * i;
+        p[0] = __floats2half2_rn(v.x, v.y);
+        p[1] = __floats2half2_rn(v.z, v.w);
+    } else {
+        reinterpret_cast<float4 *>(base)[i] = v;
+    }
+}
+
+// ==========================================================================
+// G-buffer: closest hit through each pixel centre; empty on miss / back face
+// ==========================================================================
+__global__ void __launch_bounds__(128) gbuffer_kernel(SceneView s, CamArgs c, int brute, float4 *pos, void *nrm,
+                                                      void *alb, int fmt, int *status)
+{
+    int x = blockIdx.x * 16 + (threadIdx.x & 15), y = blockIdx.y * 8 + (threadIdx.x >> 4);
+    if (x >= c.width || y >= c.height) return;
+    int64_t p = (int64_t)y * c.width + x;
+    float sx = 2.0f * ((float)x + 0.5f) / (float)c.width - 1.0f;
+    float sy = 1.0f - 2.0f * ((float)y + 0.5f) / (float)c.height;
+    float3 f = make_float3(c.f[0], c.f[1], c.f[2]), r = make_float3(c.r[0], c.r[1], c.r[2]),
+           u = make_float3(c.u[0], c.u[1], c.u[2]);
+    float3 d = f + r * (sx * c.th) + u * (sy * c.tv);
+    Ray ray = make_ray(make_float3(c.eye[0], c.eye[1], c.eye[2]), d);
+    float t;
+    int k = brute ? closest_brute(s, ray, 0.0f, t) : closest_hit(s, ray, 0.0f, t, status);
+    if (k >= 0) {
+        float4 n = __ldg(s.nrm + k);
+        if (dot(d, f3(n)) < 0.0f) {
+            float3 hp = ray.o + d * t;
+            pos[p] = make_float4(hp.x, hp.y, hp.z, __int_as_float(k));
+            store_attr_g(nrm, p, make_float4(n.x, n.y, n.z, 0.0f), fmt);
+            float4 a = __ldg(s.rho + k);
+            store_attr_g(alb, p, make_float4(a.x, a.y, a.z, 0.0f), fmt);
+            return;
+        }
+    }
+    pos[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
+    store_attr_g(nrm, p, make_float4(0, 0, 0, 0), fmt);
+    store_attr_g(alb, p, make_float4(0, 0, 0, 0), fmt);
+}
+
+cudaError_t gbuffer_build(const Exec &ex, const SceneView &s, const CamArgs &c, bool brute, float4 *pos,
+                          void *nrm, void *alb, int fmt)
+{
+    if ((int64_t)c.width * c.height == 0) return cudaSuccess;
+    dim3 grid((c.width + 15) / 16, (c.height + 7) / 8);
+    gbuffer_kernel<<<grid, 128, 0, ex.stream>>>(s, c, brute ? 1 : 0, pos, nrm, alb, fmt, ex.status);
+    VPL_LAUNCHED(ex);
+    return cudaSuccess;
+}
+
+// ==========================================================================
+// gather
+// ==========================================================================
+struct GatherExtra {
+    int *tile_counter;
+    int n_tiles, tiles_x;
+    unsigned long long *counters; // COUNT
+    const int32_t *dbg_pixels;    // DEBUG: pixel list, else null
+    int64_t n_dbg;
+    int8_t *dbg_vis;
+};
+
+template <int VIS, int PREC, bool COUNT, bool DEBUG>
+__global__ void __launch_bounds__(kGatherWarps * 32) gather_kernel(SceneView s, GatherArgs a, GatherExtra e, int *status)
+{
+    __shared__ float4 stage[kGatherWarps][3][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gfmt = PREC == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
+    const int M = a.count;
+    const float eps = a.ray_eps, d2min = a.d2_min;
+    WarpCounters wc = {0u, 0u};
+    unsigned long long n_pairs = 0, n_rays = 0, n_blocked = 0;
+    while (true) {
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(e.tile_counter, 1);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= e.n_tiles) break;
+        int64_t p;
+        bool inb; // pixel exists (in the image / in the debug list)
+        if (DEBUG) {
+            int64_t q = (int64_t)tile * 32 + lane;
+            inb = q < e.n_dbg;
+            p = inb ? e.dbg_pixels[q] : 0;
+        } else {
+            int px = (tile % e.tiles_x) * kTileW + (lane & (kTileW - 1));
+            int py = (tile / e.tiles_x) * kTileH + (lane / kTileW);
+            inb = px < a.width && py < a.height;
+            p = inb ? (int64_t)py * a.width + px : 0;
+        }
+        float4 gp = inb ? __ldg(a.g_pos + p) : make_float4(0, 0, 0, __int_as_float(-1));
+        const bool valid = inb && __float_as_int(gp.w) >= 0;
+        float4 gn = valid ? load_attr(a.g_nrm, p, gfmt) : make_float4(0, 0, 0, 0);
+        const float3 y = f3(gp), ny = f3(gn);
+        const float3 o = y + ny * eps;
+        float ax = 0.0f, ay = 0.0f, az = 0.0f; // running sums
+        float cx = 0.0f, cy_ = 0.0f, cz = 0.0f; // Kahan compensation
+        for (int base = 0; base < M; base += 32) {
+            // a latched device error (e.g. a traversal limit) ends the launch early
+            int st = lane == 0 ? *(volatile int *)status : 0;
+            if (__shfl_sync(kFull, st, 0) != 0) break;
+            const int i = base + lane;
+            if (i < M) {
+                stage[wid][0][lane] = __ldg(a.v_pos + i);
+                stage[wid][1][lane] = load_attr(a.v_nrm, i, gfmt);
+                stage[wid][2][lane] = load_attr(a.v_flux, i, gfmt);
+            }
+            __syncwarp();
+            const int cnt = min(32, M - base);
+            for (int j = 0; j < cnt; j++) {
+                const float4 xp = stage[wid][0][j], xn = stage[wid][1][j], xf = stage[wid][2][j];
+                const float3 d = f3(xp) - y;
+                const float d2 = dot(d, d);
+                const float cosy = dot(ny, d), cosi = -dot(f3(xn), d);
+                const bool lit = xf.x != 0.0f || xf.y != 0.0f || xf.z != 0.0f;
+                const bool want = valid && lit && cosy > 0.0f && cosi > 0.0f && d2 > 0.0f;
+                bool vis = true;
+                if (VIS == VPL_VIS_BVH) {
+                    const float3 q = f3(xp) + f3(xn) * eps;
+                    vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), status, wc);
+                } else if (VIS == VPL_VIS_BRUTE) {
+                    const float3 q = f3(xp) + f3(xn) * eps;
+                    vis = !warp_occluded_brute<COUNT>(s, want, make_ray(o, q - o), wc);
+                }
+                if (COUNT) {
+                    n_pairs += valid ? 1 : 0;
+                    n_rays += want ? 1 : 0;
+                    n_blocked += (want && !vis) ? 1 : 0;
+                }
+                if (DEBUG && inb) e.dbg_vis[((int64_t)tile * 32 + lane) * M + base + j] = want ? (vis ? 1 : 0) : -1;
+                if (want && vis) {
+                    const float g = __fdividef(cosi * cosy, d2 * fmaxf(d2, d2min));
+                    if (PREC == VPL_PREC_FP16_KAHAN) {
+                        float yv = fmaf(xf.x, g, -cx), t = __fadd_rn(ax, yv);
+                        cx = __fsub_rn(__fsub_rn(t, ax), yv); ax = t;
+                        yv = fmaf(xf.y, g, -cy_); t = __fadd_rn(ay, yv);
+                        cy_ = __fsub_rn(__fsub_rn(t, ay), yv); ay = t;
+                        yv = fmaf(xf.z, g, -cz); t = __fadd_rn(az, yv);
+                        cz = __fsub_rn(__fsub_rn(t, az), yv); az = t;
+                    } else {
+                        ax = fmaf(xf.x, g, ax);
+                        ay = fmaf(xf.y, g, ay);
+                        az = fmaf(xf.z, g, az);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (!DEBUG && inb) {
+            float4 rho = valid ? load_attr(a.g_alb, p, gfmt) : make_float4(0, 0, 0, 0);
+            const float k = 1.0f / (kPi * kPi);
+            a.out[p] = make_float4(rho.x * ax * k, rho.y * ay * k, rho.z * az * k, 0.0f);
+        }
+    }
+    if (COUNT) {
+        unsigned long long v[5] = {n_pairs, n_rays, (unsigned long long)wc.visits, (unsigned long long)wc.tests,
+                                   n_blocked};
+        for (int k = 0; k < 5; k++) {
+            unsigned long long x = v[k];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(kFull, x, off);
+            if (lane == 0) atomicAdd(e.counters + k, x);
+        }
+    }
+}
+
+template <int VIS, int PREC, bool COUNT, bool DEBUG>
+static cudaError_t launch_gather(const Exec &ex, const SceneView &s, const GatherArgs &a, GatherExtra e)
+{
+    auto kern = gather_kernel<VIS, PREC, COUNT, DEBUG>;
+    int dev = 0, sms = 0, per_sm = 0;
+    VPL_TRY(cudaGetDevice(&dev));
+    VPL_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    VPL_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherWarps * 32, 0));
+    int64_t want = (e.n_tiles + kGatherWarps - 1) / kGatherWarps;
+    int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    unsigned grid = (unsigned)(want < cap ? want : cap);
+    if (grid == 0) grid = 1;
+    kern<<<grid, kGatherWarps * 32, 0, ex.stream>>>(s, a, e, ex.status);
+    VPL_LAUNCHED(ex);
+    return cudaSuccess;
+}
+
+template <bool COUNT, bool DEBUG>
+static cudaError_t dispatch(const Exec &ex, const SceneView &s, const GatherArgs &a, GatherExtra e)
+{
+#define VPL_CASE(V, P)                                                                  \
+    if (a.visibility == V && a.precision == P) return launch_gather<V, P, COUNT, DEBUG>(ex, s, a, e);
+    VPL_CASE(VPL_VIS_BVH, VPL_PREC_FP32)
+    VPL_CASE(VPL_VIS_BRUTE, VPL_PREC_FP32)
+    VPL_CASE(VPL_VIS_NONE, VPL_PREC_FP32)
+#undef VPL_CASE
+    return cudaErrorInvalidValue;
+}
+
+static cudaError_t run_gather(const Exec &ex, const SceneView &s, const GatherArgs &a, bool count,
+                              unsigned long long *counters, const int32_t *pixels, int64_t n_pixels, int8_t *vis)
+{
+    const int64_t npx = (int64_t)a.width * a.height;
+    if (pixels == nullptr && npx == 0) return cudaSuccess;
+    if (pixels != nullptr && n_pixels == 0) return cudaSuccess;
+    Tmp ctr;
+    VPL_TRY(ctr.alloc(ex, sizeof(int)));
+    VPL_TRY(cudaMemsetAsync(ctr.p, 0, sizeof(int), ex.stream));
+    GatherExtra e;
+    e.tile_counter = ctr.as<int>();
+    e.tiles_x = (a.width + kTileW - 1) / kTileW;
+    e.n_tiles = pixels ? (int)((n_pixels + 31) / 32) : e.tiles_x * ((a.height + kTileH - 1) / kTileH);
+    e.counters = counters;
+    e.dbg_pixels = pixels;
+    e.n_dbg = n_pixels;
+    e.dbg_vis = vis;
+    if (pixels) return dispatch<false, true>(ex, s, a, e);
+    if (count) return dispatch<true, false>(ex, s, a, e);
+    return dispatch<false, false>(ex, s, a, e);
+}
+
+cudaError_t gather(const Exec &ex, const SceneView &s, const GatherArgs &a)
+{
+    return run_gather(ex, s, a, false, nullptr, nullptr, 0, nullptr);
+}
+
+cudaError_t gather_counters(const Exec &ex, const SceneView &s, const GatherArgs &a, unsigned long long *counters)
+{
+    VPL_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 5, ex.stream));
+    return run_gather(ex, s, a, true, counters, nullptr, 0, nullptr);
+}
+
+cudaError_t gather_visibility(const Exec &ex, const SceneView &s, const GatherArgs &a, const int32_t *pixels,
+                              int64_t n_pixels, int8_t *vis)
+{
+    return run_gather(ex, s, a, false, nullptr, pixels, n_pixels, vis);
+}
+
+// ==========================================================================
+// diagnostics
+// ==========================================================================
+__global__ void philox_kernel(const uint64_t *ctr, const uint64_t *key, int64_t n, uint64_t *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    philox4x64_10(c, key[2 * i], key[2 * i + 1]);
+    for (int k = 0; k < 4; k++) out[4 * i + k] = c[k];
+}
+
+cudaError_t debug_philox(const Exec &ex, const uint64_t *ctr, const uint64_t *key, int64_t n, uint64_t *out)
+{
+    if (n == 0) return cudaSuccess;
+    philox_kernel<<<grid_for(n, 256), 256, 0, ex.stream>>>(ctr, key, n, out);
+    VPL_LAUNCHED(ex);
+    return cudaSuccess;
+}
+
+__global__ void rays_kernel(SceneView s, int mode, int brute, const float4 *a, const float4 *b, int64_t n,
+                            int32_t *out_tri, float *out_t, int *status)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float3 p = f3(a[i]), q = f3(b[i]);
+    if (mode == 0) {
+        Ray r = make_ray(p, q - p);
+        bool bl = brute ? occluded_brute(s, r) : occluded1(s, r, status);
+        out_tri[i] = bl ? 1 : 0;
+    } else {
+        Ray r = make_ray(p, q);
+        float t;
+        int k = brute ? closest_brute(s, r, 0.0f, t) : closest_hit(s, r, 0.0f, t, status);
+        out_tri[i] = k;
+        if (out_t) out_t[i] = k >= 0 ? t : 0.0f;
+    }
+}
+
+cudaError_t debug_rays(const Exec &ex, const SceneView &s, int mode, int brute, const float4 *a, const float4 *b,
+                       int64_t n, int32_t *out_tri, float *out_t)
+{
+    if (n == 0) return cudaSuccess;
+    rays_kernel<<<grid_for(n, 128), 128, 0, ex.stream>>>(s, mode, brute, a, b, n, out_tri, out_t, ex.status);
+    VPL_LAUNCHED(ex);
+    return cudaSuccess;
+}
+
+} // namespace vpl

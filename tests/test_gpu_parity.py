@@ -1,0 +1,357 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (Jin et al., arXiv 2203.11484, Sec. 3 and Eqs. 1-2).
+
+  Philox words, close-range sets, patch triangle assignment, VPL tags: bit-exact
+  VPL positions: within 1e-6 of the scene diagonal; fluxes: 1e-6 relative
+  pixels: |gpu - ref| <= 1e-4 |ref| + 1e-7 mean(ref), except pixels whose
+  error is explained by visibility flips (<= 1e-5 of the pairs, each within
+  1e-5 of the scene diagonal of an edge or plane)
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2203_11484_gb300 import workloads as W
+import parity as PY
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11484_gb300 import build, vpl
+    build.build_library()
+    return vpl
+
+
+@pytest.fixture(scope="module")
+def ctx(V):
+    c = V.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def cornell(V, ctx, orc):
+    wl = W.cornell_workload()
+    sid = ctx.upload(wl.scene)
+    return wl, sid, orc.OracleScene(wl.scene)
+
+
+@pytest.fixture(scope="module")
+def room(V, ctx, orc):
+    wl = W.room200k_workload()
+    sid = ctx.upload(wl.scene)
+    return wl, sid, orc.OracleScene(wl.scene)
+
+
+def _dev(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# ---------------------------------------------------------------------------
+# random numbers: Philox4x64-10 words bit-exact
+# ---------------------------------------------------------------------------
+def test_philox_bit_exact(V, ctx, orc):
+    rng = np.random.default_rng(2)
+    n = 4096
+    ctr = rng.integers(0, 2**63, size=(n, 4), dtype=np.uint64)
+    ctr[:64, 2:] = 0
+    ctr[:64, 0] = np.arange(64)
+    key = rng.integers(0, 2**63, size=(n, 2), dtype=np.uint64)
+    out = torch.zeros((n, 4), dtype=torch.int64, device="cuda")
+    V.vpl_debug_philox(ctx.h, _dev(ctr.view(np.int64)), _dev(key.view(np.int64)), out)
+    V.vpl_sync(ctx.h)
+    got = out.cpu().numpy().view(np.uint64)
+    for i in range(0, n, 7):
+        assert np.array_equal(got[i], orc.philox4x64_10(ctr[i], key[i])), i
+
+
+# ---------------------------------------------------------------------------
+# BVH queries against the oracle (brute force and its own FP64 BVH)
+# ---------------------------------------------------------------------------
+def _ray_queries(V, ctx, sid, P, Q, mode, brute):
+    n = P.shape[0]
+    a = np.zeros((n, 4), np.float32)
+    b = np.zeros((n, 4), np.float32)
+    a[:, :3], b[:, :3] = P, Q
+    tri = torch.zeros(n, dtype=torch.int32, device="cuda")
+    t = torch.zeros(n, dtype=torch.float32, device="cuda")
+    V.vpl_debug_rays(ctx.h, sid, mode, brute, _dev(a), _dev(b), tri, t)
+    V.vpl_sync(ctx.h)
+    return tri.cpu().numpy(), t.cpu().numpy()
+
+
+@pytest.mark.parametrize("which", ["cornell", "room"])
+def test_bvh_visibility_and_closest_hit(V, ctx, which, request):
+    wl, sid, osc = request.getfixturevalue(which)
+    sc = wl.scene
+    Ld = sc.diag()
+    rng = np.random.default_rng(11)
+    lo, hi = sc.verts.min(0), sc.verts.max(0)
+    n = 20000
+    P = rng.uniform(lo, hi, size=(n, 3)).astype(np.float32)
+    Q = rng.uniform(lo, hi, size=(n, 3)).astype(np.float32)
+    # segments occluded test
+    for brute in ([0, 1] if which == "cornell" else [0]):
+        occ, _ = _ray_queries(V, ctx, sid, P, Q, 0, brute)
+        ref = osc.occluded(P.astype(np.float64), Q.astype(np.float64), vis_mode=0)
+        diff = np.nonzero((occ != 0) != ref)[0]
+        assert len(diff) <= max(2, int(1e-3 * n)), (brute, len(diff))
+        for i in diff:
+            assert osc.segment_margin(P[i], Q[i]) <= PY.FLIP_MARGIN * Ld
+    # closest hit along P + t (Q - P)
+    D = (Q - P).astype(np.float32)
+    tri, t = _ray_queries(V, ctx, sid, P, D, 1, 0)
+    rtri, rt = osc.closest(P.astype(np.float64), D.astype(np.float64), 0.0, 0)
+    same = tri == rtri
+    assert same.mean() > 0.999
+    hit = same & (tri >= 0)
+    assert np.allclose(t[hit], rt[hit], rtol=1e-5, atol=1e-6)
+    for i in np.nonzero(~same)[0]:
+        # different triangle: the ray grazes an edge, or two hits are at equal t
+        near_tie = (tri[i] >= 0 and rtri[i] >= 0 and abs(t[i] - rt[i]) <= 1e-5 * max(1.0, rt[i]))
+        q = P[i] + D[i] * (rt[i] if rtri[i] >= 0 else t[i])
+        assert near_tie or osc.segment_margin(P[i], P[i] + 2 * (q - P[i])) <= PY.FLIP_MARGIN * Ld
+
+
+# ---------------------------------------------------------------------------
+# G-buffer (points y of Eq. 1)
+# ---------------------------------------------------------------------------
+def _gbuffer(V, ctx, sid, cam):
+    gb = V.GBuffer.empty(cam.width, cam.height)
+    V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
+    V.vpl_sync(ctx.h)
+    pos = gb.pos.cpu().numpy()
+    return dict(pos=pos[:, :3].astype(np.float64), tri=pos[:, 3].copy().view(np.int32).astype(np.int64),
+                nrm=gb.nrm.cpu().numpy()[:, :3].astype(np.float64),
+                rho=gb.albedo.cpu().numpy()[:, :3].astype(np.float64)), gb
+
+
+@pytest.mark.parametrize("which", ["cornell", "room"])
+def test_gbuffer_parity(V, ctx, which, request):
+    wl, sid, osc = request.getfixturevalue(which)
+    cam = wl.views[0].camera
+    g, _ = _gbuffer(V, ctx, sid, cam)
+    npx = cam.width * cam.height
+    pix = np.arange(npx) if which == "cornell" else np.random.default_rng(3).choice(npx, 8192, replace=False)
+    ref = osc.gbuffer(cam, pix)
+    Ld = wl.scene.diag()
+    same = g["tri"][pix] == ref["tri"]
+    assert same.mean() >= 0.999
+    ok = same & (ref["tri"] >= 0)
+    assert np.abs(g["pos"][pix][ok] - ref["pos"][ok]).max() <= PY.POS_TOL * Ld
+    assert np.abs(g["nrm"][pix][ok] - ref["nrm"][ok]).max() <= 1e-7
+    assert np.array_equal(g["rho"][pix][ok], ref["rho"][ok])
+    # pixels that hit another triangle: the primary ray passes an edge
+    frame_eye = np.array(cam.eye, np.float64)
+    for k in np.nonzero(~same)[0]:
+        q = ref["pos"][k] if ref["tri"][k] >= 0 else g["pos"][pix[k]]
+        far = frame_eye + 1.01 * (q - frame_eye)
+        assert osc.segment_margin(frame_eye, far) <= PY.FLIP_MARGIN * Ld * 10
+
+
+# ---------------------------------------------------------------------------
+# VPL generation (Sec. 3 pipeline steps (1)-(3))
+# ---------------------------------------------------------------------------
+def _generate(V, ctx, sid, cam, gen):
+    M = gen.m_close + gen.m_far
+    vs = V.VplSet.empty(M)
+    V.vpl_generate(ctx.h, sid, cam, gen, vs)
+    rc = V.vpl_sync(ctx.h, check=False)
+    info = V.vpl_generate_info(ctx.h)
+    pos = vs.pos.cpu().numpy()
+    nrm = vs.nrm.cpu().numpy()
+    return dict(pos=pos[:, :3].astype(np.float64), tri=pos[:, 3].copy().view(np.int32).astype(np.int64),
+                nrm=nrm[:, :3].astype(np.float64), tag=nrm[:, 3].copy().view(np.int32).astype(np.int64),
+                flux=vs.flux.cpu().numpy()[:, :3].astype(np.float64), status=rc, info=info), vs
+
+
+def _light_flip_ok(osc, wl, gen, k, x, n):
+    """A patch VPL whose single light sample's visibility differs: the shadow
+    segment must graze an edge / plane."""
+    import oracle as O
+    L = wl.scene.light
+    w = O.philox4x64_10([k, 0, 0, 0], [gen.seed, 2])
+    s1, s2 = (w[0] >> np.uint64(40)) / 16777216.0, (w[1] >> np.uint64(40)) / 16777216.0
+    c = np.array(L.center, np.float64)
+    y = c + (2 * s1 - 1) * 0.5 * np.array(L.edge_u) + (2 * s2 - 1) * 0.5 * np.array(L.edge_v)
+    xo = x + n * float(np.float32(gen.ray_eps))
+    return osc.segment_margin(xo, y) <= PY.FLIP_MARGIN * wl.scene.diag()
+
+
+@pytest.mark.parametrize("which", ["cornell", "room"])
+def test_generate_parity(V, ctx, which, request):
+    wl, sid, osc = request.getfixturevalue(which)
+    view = wl.views[0]
+    cam, gen = view.camera, view.gen
+    g, _ = _generate(V, ctx, sid, cam, gen)
+    r = osc.generate(cam, gen, vis_mode=0)
+    assert g["status"] == 0 and r["status"] == 0
+    info = g["info"]
+    # (1) + (2): close set, quantised areas, strata -> triangles: exact
+    assert info["n_close"] == r["n_close"]
+    assert info["f_total"] == r["f_total"] and info["shift_s"] == r["shift_s"]
+    Mc = gen.m_close
+    assert np.array_equal(g["tri"][:Mc], r["tri"][:Mc])
+    assert np.array_equal(g["tag"][:Mc], r["tag"][:Mc])
+    Ld = wl.scene.diag()
+    assert np.abs(g["pos"][:Mc] - r["pos"][:Mc]).max() <= PY.POS_TOL * Ld
+    assert np.abs(g["nrm"][:Mc] - r["nrm"][:Mc]).max() <= 1e-7
+    gf, rf = g["flux"][:Mc], r["flux"][:Mc]
+    bad = np.nonzero((np.abs(gf - rf) > PY.FLUX_RTOL * np.abs(rf) + 1e-30).any(axis=1))[0]
+    for k in bad:   # only light-sample visibility flips may differ
+        assert (gf[k] == 0).all() != (rf[k] == 0).all(), k
+        assert _light_flip_ok(osc, wl, gen, int(k), r["pos"][k], r["nrm"][k]), k
+    assert len(bad) <= max(1, int(0.01 * Mc))
+    # (3): light paths, matched by (path, bounce) tag
+    assert info["m_far_kept"] == r["m_far_kept"] == gen.m_far
+    gt, rt = g["tag"][Mc:], r["tag"][Mc:]
+    if info["paths"] == r["paths"] and np.array_equal(gt, rt):
+        same = g["tri"][Mc:] == r["tri"][Mc:]
+        assert same.all()
+        assert np.abs(g["pos"][Mc:] - r["pos"][Mc:]).max() <= 100 * PY.POS_TOL * Ld
+        assert np.allclose(g["flux"][Mc:], r["flux"][Mc:], rtol=PY.FLUX_RTOL, atol=0)
+    else:
+        # a light path that grazed an edge changed course: everything before
+        # it still matches exactly
+        first = int(np.argmax(gt != rt)) if not np.array_equal(gt, rt) else len(gt)
+        assert first > 0.5 * len(gt), first
+        assert abs(info["paths"] - r["paths"]) <= max(2, 0.01 * r["paths"])
+
+
+# ---------------------------------------------------------------------------
+# gather (Eq. 1) on identical FP32 inputs made by the oracle
+# ---------------------------------------------------------------------------
+def _to_gbuffer(V, g, width, height):
+    n = width * height
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, :3] = g["pos"]
+    pos[:, 3] = np.asarray(g["tri"], np.int32).view(np.float32)
+    nrm = np.zeros((n, 4), np.float32)
+    nrm[:, :3] = g["nrm"]
+    alb = np.zeros((n, 4), np.float32)
+    alb[:, :3] = g["rho"]
+    return V.GBuffer(_dev(pos), _dev(nrm), _dev(alb), width, height)
+
+
+def _to_vpls(V, v):
+    M = len(v["pos"])
+    out = []
+    for key in ("pos", "nrm", "flux"):
+        a = np.zeros((max(M, 0), 4), np.float32)
+        a[:, :3] = v[key]
+        out.append(_dev(a))
+    return V.VplSet(*out)
+
+
+def _gather(V, ctx, sid, gbuf, vpls, params):
+    out = torch.zeros((gbuf.width * gbuf.height, 4), dtype=torch.float32, device="cuda")
+    V.vpl_gather(ctx.h, sid, gbuf, vpls, params, out)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    return out.cpu().numpy()
+
+
+def _check_gather(V, ctx, sid, osc, wl, gb_ref, vpl_ref, width, height, params, oracle_vis):
+    g, v = PY.oracle_inputs_f32(gb_ref, vpl_ref)
+    gbuf = _to_gbuffer(V, g, width, height)
+    vpls = _to_vpls(V, v)
+    got = _gather(V, ctx, sid, gbuf, vpls, params)
+    ref = osc.gather(g, v, params.d2_min, params.ray_eps, vis_mode=oracle_vis)
+    bad = np.nonzero(PY.pixel_fail(got, ref))[0]
+    n_pairs = int((g["tri"] >= 0).sum()) * len(v["pos"])
+    flips_total = 0
+    if len(bad):
+        assert params.visibility != W.VIS_NONE, "no visibility: nothing may differ"
+        pix = torch.as_tensor(bad.astype(np.int32)).cuda()
+        vis = torch.zeros((len(bad), len(v["pos"])), dtype=torch.int8, device="cuda")
+        V.vpl_debug_visibility(ctx.h, sid, gbuf, vpls, params, pix, vis)
+        V.vpl_sync(ctx.h)
+        vis = vis.cpu().numpy()
+        Ld = wl.scene.diag()
+        for row, p in enumerate(bad):
+            nf, ok, _ = PY.explain_pixel(osc, g["pos"][p], g["nrm"][p], v, vis[row], params.d2_min,
+                                         float(np.float32(params.ray_eps)), Ld)
+            assert nf > 0 and ok, (p, got[p], ref[p], nf)
+            flips_total += nf
+    assert flips_total <= max(3, PY.FLIP_FRACTION * n_pairs), flips_total
+    return got, ref, len(bad)
+
+
+@pytest.mark.parametrize("vis", [W.VIS_BRUTE, W.VIS_BVH, W.VIS_NONE])
+def test_gather_parity_cornell(V, ctx, cornell, vis):
+    wl, sid, osc = cornell
+    view = wl.views[0]
+    gb = osc.gbuffer(view.camera, vis_mode=1)
+    vp = osc.generate(view.camera, view.gen, vis_mode=1)
+    params = W.GatherParams(view.gather.d2_min, view.gather.ray_eps, W.PREC_FP32, vis)
+    ovis = {W.VIS_BRUTE: 1, W.VIS_BVH: 0, W.VIS_NONE: 2}[vis]
+    got, ref, nbad = _check_gather(V, ctx, sid, osc, wl, gb, vp, view.camera.width, view.camera.height,
+                                   params, ovis)
+    assert ref.max() > 0 and np.isfinite(got).all()
+
+
+def test_gather_parity_room_sampled(V, ctx, room):
+    """The 200k-triangle room with 4096 VPLs: 2048 sampled receivers laid out
+    as a 64 x 32 G-buffer (every pixel is independent in Eq. 1)."""
+    wl, sid, osc = room
+    view = wl.views[0]
+    cam = view.camera
+    pix = np.random.default_rng(5).choice(cam.width * cam.height, 2048, replace=False)
+    gb = osc.gbuffer(cam, pix)
+    vp = osc.generate(cam, view.gen, vis_mode=0)
+    got, ref, nbad = _check_gather(V, ctx, sid, osc, wl, gb, vp, 64, 32, view.gather, 0)
+    assert ref.max() > 0
+
+
+# ---------------------------------------------------------------------------
+# the whole pipeline (steps (1)-(4)) through vpl_render
+# ---------------------------------------------------------------------------
+def _render(V, ctx, sid, view):
+    cam = view.camera
+    out = torch.zeros((cam.width * cam.height, 4), dtype=torch.float32, device="cuda")
+    V.vpl_render(ctx.h, sid, cam, view.gen, view.gather, out)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    return out.cpu().numpy()
+
+
+def _render_parity(V, ctx, sid, osc, wl, view, pix):
+    import oracle as O
+    img = _render(V, ctx, sid, view)
+    r = O.render(osc, view, pix)
+    # pixels whose primary ray hits another triangle are G-buffer flips
+    g, _ = _gbuffer(V, ctx, sid, view.camera)
+    same_tri = g["tri"][pix] == r["gbuffer"]["tri"]
+    assert same_tri.mean() >= 0.999
+    got = img[pix]
+    bad = PY.pixel_fail(got, r["image"]) & same_tri
+    return img, r, bad
+
+
+def test_render_parity_cornell_full(V, ctx, cornell):
+    wl, sid, osc = cornell
+    view = wl.views[0]
+    pix = np.arange(view.camera.width * view.camera.height)
+    img, r, bad = _render_parity(V, ctx, sid, osc, wl, view, pix)
+    # tiny scene, brute-force visibility: at most a handful of flip pixels
+    assert bad.sum() <= 3, np.nonzero(bad)[0][:10]
+    assert r["image"].max() > 0
+
+
+def test_render_parity_room_full_size(V, ctx, room):
+    """Full 1024 x 1024, 4096-VPL render (the benchmark's launch), sampled
+    pixels checked against the oracle."""
+    wl, sid, osc = room
+    view = wl.views[0]
+    pix = np.random.default_rng(9).choice(view.camera.width * view.camera.height, 512, replace=False)
+    img, r, bad = _render_parity(V, ctx, sid, osc, wl, view, pix)
+    assert bad.mean() <= 0.01, np.nonzero(bad)[0][:10]
+    assert np.isfinite(img).all()
