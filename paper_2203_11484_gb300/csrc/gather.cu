@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) gather_kernel(SceneView s, 
             }
             __syncwarp();
         }
-        if (!DEBUG && inb) {
+        if (!DEBUG && inb && a.out) {
             float4 rho = valid ? load_attr(a.g_alb, p, gfmt) : make_float4(0, 0, 0, 0);
             const float k = 1.0f / (kPi * kPi);
             a.out[p] = make_float4(rho.x * ax * k, rho.y * ay * k, rho.z * az * k, 0.0f);
