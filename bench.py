@@ -196,7 +196,8 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     B.build_library()
 
-    wl = W.room200k_workload(seed=1 + rank)  # each rank renders its own close-up view
+    wl = W.room200k_workload(width=args.width, height=args.height, m_total=args.vpls,
+                             seed=1 + rank)  # each rank renders its own close-up view
     view = wl.views[0]
     cam, gen, gat = view.camera, view.gen, view.gather
     M = gen.m_close + gen.m_far
@@ -296,7 +297,8 @@ def run_ours(args):
                 "kernel": "gather_kernel<BVH,FP32>",
                 "peak_note": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz",
                 "counters": {"pairs": cnt[0], "shadow_rays": cnt[1], "node_visits": cnt[2],
-                             "tri_tests": cnt[3], "blocked": cnt[4]},
+                             "tri_tests": cnt[3], "blocked": cnt[4], "warp_steps": cnt[5],
+                             "lane_utilisation": cnt[2] / max(1, 32 * cnt[5])},
                 "gather_ms": gather_in_step_ms,
                 "flops_per_unit": {"pair": FLOPS_PER_PAIR, "ray": FLOPS_PER_RAY, "node": FLOPS_PER_NODE,
                                    "tri": FLOPS_PER_TRI}}
@@ -367,6 +369,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--width", type=int, default=1024)
+    ap.add_argument("--height", type=int, default=1024)
+    ap.add_argument("--vpls", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -232,12 +232,13 @@ VPL_API int vpl_set_timing(vpl_ctx *ctx, int32_t on);
 VPL_API int vpl_stage_times(vpl_ctx *ctx, float *ms, int32_t n);
 /* Kernel launches enqueued by this context since its creation. */
 VPL_API int64_t vpl_launch_count(const vpl_ctx *ctx);
-/* Work counters of one gather launch (not timed): out[0] pairs evaluated,
- * [1] pairs with a non-zero shading term (shadow rays), [2] BVH node visits
- * summed over rays, [3] triangle tests summed over rays, [4] blocked rays. */
+/* Work counters of one gather launch (not timed): out[0] pairs with a
+ * non-empty receiver, [1] pairs with a non-zero shading term (shadow rays),
+ * [2] BVH node visits summed over rays, [3] triangle tests summed over rays,
+ * [4] blocked rays, [5] warp-wide packet traversal steps. */
 VPL_API int vpl_gather_counters(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf,
-                        const vpl_vpl_set *vpls, const vpl_gather_params *params,
-                        uint64_t out[5], vpl_stream stream);
+                                const vpl_vpl_set *vpls, const vpl_gather_params *params,
+                                uint64_t out[6], vpl_stream stream);
 
 #ifdef __cplusplus
 }

@@ -629,7 +629,7 @@ int vpl_stage_times(vpl_ctx *ctx, float *ms, int32_t n)
 int64_t vpl_launch_count(const vpl_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
 int vpl_gather_counters(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf, const vpl_vpl_set *vpls,
-                        const vpl_gather_params *params, uint64_t out[5], vpl_stream stream)
+                        const vpl_gather_params *params, uint64_t out[6], vpl_stream stream)
 {
     if (!ctx || !out) return VPL_ERR_INVALID_ARG;
     SceneRec *s = find_scene(ctx, scene);
@@ -641,15 +641,15 @@ int vpl_gather_counters(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbu
     DeviceGuard g(ctx->device);
     Exec ex = exec_of(ctx, stream);
     unsigned long long *d = nullptr;
-    CK(ctx, cudaMallocFromPoolAsync((void **)&d, sizeof(unsigned long long) * 5, ctx->pool, ex.stream),
+    CK(ctx, cudaMallocFromPoolAsync((void **)&d, sizeof(unsigned long long) * 6, ctx->pool, ex.stream),
        "vpl_gather_counters");
     cudaError_t e = gather_counters(ex, view_of(s), gather_args(gbuf, vpls, params, nullptr), d);
-    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, ex.stream);
     cudaFreeAsync(d, ex.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ex.stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "vpl_gather_counters");
-    for (int k = 0; k < 5; k++) out[k] = h[k];
+    for (int k = 0; k < 6; k++) out[k] = h[k];
     return VPL_OK;
 }
 

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) gather_kernel(SceneView s, 
     const int gfmt = PREC == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     const int M = a.count;
     const float eps = a.ray_eps, d2min = a.d2_min;
-    WarpCounters wc = {0u, 0u};
+    WarpCounters wc = {0u, 0u, 0u};
     unsigned long long n_pairs = 0, n_rays = 0, n_blocked = 0;
     while (true) {
         int tile = 0;
@@ -184,9 +184,9 @@ __global__ void __launch_bounds__(kGatherWarps * 32) gather_kernel(SceneView s, 
         }
     }
     if (COUNT) {
-        unsigned long long v[5] = {n_pairs, n_rays, (unsigned long long)wc.visits, (unsigned long long)wc.tests,
-                                   n_blocked};
-        for (int k = 0; k < 5; k++) {
+        unsigned long long v[6] = {n_pairs, n_rays, (unsigned long long)wc.visits, (unsigned long long)wc.tests,
+                                   n_blocked, lane == 0 ? (unsigned long long)wc.steps : 0ULL};
+        for (int k = 0; k < 6; k++) {
             unsigned long long x = v[k];
             for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(kFull, x, off);
             if (lane == 0) atomicAdd(e.counters + k, x);
@@ -252,7 +252,7 @@ cudaError_t gather(const Exec &ex, const SceneView &s, const GatherArgs &a)
 
 cudaError_t gather_counters(const Exec &ex, const SceneView &s, const GatherArgs &a, unsigned long long *counters)
 {
-    VPL_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 5, ex.stream));
+    VPL_TRY(cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * 6, ex.stream));
     return run_gather(ex, s, a, true, counters, nullptr, 0, nullptr);
 }
 

@@ -367,7 +367,8 @@ __device__ __forceinline__ bool occluded_brute(const SceneView &s, const Ray &r)
 // (one transaction, broadcast).
 // --------------------------------------------------------------------------
 struct WarpCounters {
-    uint32_t visits, tests;
+    uint32_t visits, tests; // per lane: nodes visited / triangles tested by its own ray
+    uint32_t steps;         // per warp: packet traversal steps (same in every lane)
 };
 
 template <bool COUNT>
@@ -402,7 +403,10 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
         slab2(r, n0, n1, n2, 0.0f, 1.0f, h0, h1, t0, t1);
         h0 = h0 && live;
         h1 = h1 && live;
-        if (COUNT && live) wc.visits++;
+        if (COUNT) {
+            wc.steps++;
+            if (live) wc.visits++;
+        }
         int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
         if (c0 < 0) {
             if (__any_sync(kFull, h0)) leaf_any<COUNT>(s, r, ~c0, __float_as_int(n3.z), h0, occl, wc);
@@ -449,6 +453,7 @@ __device__ __forceinline__ bool warp_occluded_brute(const SceneView &s, bool wan
     bool occl = false;
     for (int k = 0; k < s.n_tris; k++) {
         if (__ballot_sync(kFull, want && !occl) == 0) break;
+        if (COUNT) wc.steps++;
         float4 v0 = __ldg(s.tri + 3 * k), e1 = __ldg(s.tri + 3 * k + 1), e2 = __ldg(s.tri + 3 * k + 2);
         if (want && !occl) {
             float t;

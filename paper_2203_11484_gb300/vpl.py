@@ -362,7 +362,7 @@ def vpl_launch_count(ctx) -> int:
 def vpl_gather_counters(ctx, scene: int, gbuf: GBuffer, vpls: VplSet, params: W.GatherParams,
                         stream=None) -> list:
     gb, vs, p = gbuf.struct(), vpls.struct(), make_gather(params)
-    out = (C.c_uint64 * 5)()
+    out = (C.c_uint64 * 6)()
     _check(ctx, load().vpl_gather_counters(ctx, scene, C.byref(gb), C.byref(vs), C.byref(p), out,
                                            _stream(stream)), "vpl_gather_counters")
     return [int(v) for v in out]
