@@ -195,6 +195,27 @@ VPL_API int vpl_gather(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf
                const vpl_vpl_set *vpls, const vpl_gather_params *params, float *out_rgba,
                vpl_stream stream);
 
+/* vpl_gather for callers that must not allocate device memory.  The paper has
+ * no counterpart to this entry point.  It exists for callers that reserve
+ * their device memory up front and may not allocate while they run -- a
+ * render loop working inside a fixed memory budget owned by its host
+ * application, or code where an allocation could block on or synchronise
+ * with other work on the device.  Arguments, results and errors are those of
+ * vpl_gather; the caller passes every input and output buffer, and this call
+ * makes no cudaMalloc/cudaFree, pool or other allocating call.
+ * Its one piece of scratch, the tile counter of the gather's dynamic
+ * scheduler, sits in a 256-byte static device array of the library that
+ * every GPU which loads libvpl holds until the process exits.  The first
+ * call on each device looks up that array's device address with the
+ * context's device current; make that first call before any stream capture.
+ * Each call clears the counter before its launch; all calls share the array,
+ * so calls that overlap on the GPU (other streams, other contexts on the same
+ * device) race on it and must be ordered by the caller.  Images of more than
+ * 2^30 tiles of 8 x 4 pixels return VPL_ERR_INVALID_ARG. */
+VPL_API int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf,
+                               const vpl_vpl_set *vpls, const vpl_gather_params *params,
+                               float *out_rgba, vpl_stream stream);
+
 /* Steps (1)-(4) with library-held temporaries: G-buffer, VPLs, gather. */
 VPL_API int vpl_render(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam,
                const vpl_gen_params *gen, const vpl_gather_params *params, float *out_rgba,

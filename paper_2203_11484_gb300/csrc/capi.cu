@@ -499,6 +499,28 @@ int vpl_gather(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf, const 
     return VPL_OK;
 }
 
+int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf, const vpl_vpl_set *vpls,
+                       const vpl_gather_params *params, float *out_rgba, vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    int rc = check_gbuffer(ctx, gbuf, nullptr);
+    if (rc) return rc;
+    if ((rc = check_vpls(ctx, vpls))) return rc;
+    if ((rc = check_gather(ctx, params, gbuf->format, vpls->format))) return rc;
+    if ((int64_t)gbuf->width * gbuf->height > 0 && !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "out_rgba is NULL");
+    const int64_t tiles = (((int64_t)gbuf->width + 7) / 8) * (((int64_t)gbuf->height + 3) / 4);
+    if (tiles > gather_noalloc_max_tiles())
+        return fail(ctx, VPL_ERR_INVALID_ARG,
+                    "vpl_gather_noalloc: image has more than 2^30 tiles of 8x4 pixels, the most its static "
+                    "tile counter supports");
+    DeviceGuard g(ctx->device);
+    Exec ex = exec_of(ctx, stream);
+    CK(ctx, gather_noalloc(ex, view_of(s), gather_args(gbuf, vpls, params, out_rgba)), "vpl_gather_noalloc");
+    return VPL_OK;
+}
+
 int vpl_render(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const vpl_gen_params *gen,
                const vpl_gather_params *params, float *out_rgba, vpl_stream stream)
 {

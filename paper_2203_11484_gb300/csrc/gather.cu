@@ -9,6 +9,8 @@
 // (warp_occluded).  Tiles are handed out dynamically (an atomic counter) to a
 // grid of resident blocks.  Each pixel sums its VPLs in index order in one
 // thread, so the result does not depend on tiling or batching.
+#include <mutex>
+
 #include "vpl_internal.h"
 
 namespace vpl {
@@ -261,6 +263,53 @@ cudaError_t gather_visibility(const Exec &ex, const SceneView &s, const GatherAr
 {
     return run_gather(ex, s, a, false, nullptr, pixels, n_pixels, vis);
 }
+
+// ==========================================================================
+// gather that allocates nothing
+// ==========================================================================
+// For callers that may not allocate device memory while they run, the
+// tile counter of the dynamic scheduler lives in this file-scope array (256
+// bytes, held by every device that loads the library until the process
+// exits) instead of the context's memory pool.  All such calls share it.
+constexpr int kNoAllocScratchInts = 64;
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocScratchInts];
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static int *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+cudaError_t gather_noalloc(const Exec &ex, const SceneView &s, const GatherArgs &a)
+{
+    const int64_t npx = (int64_t)a.width * a.height;
+    if (npx == 0) return cudaSuccess;
+    int dev = 0;
+    VPL_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    int *scratch = nullptr;
+    {
+        // once per device, with that device current: host code only knows a
+        // stand-in for the array, the kernel needs its device address
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            VPL_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_addr[dev] = static_cast<int *>(p);
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    // the array keeps the previous call's counter: start this one at zero
+    VPL_TRY(cudaMemsetAsync(scratch, 0, sizeof(int), ex.stream));
+    GatherExtra e;
+    e.tile_counter = scratch;
+    e.tiles_x = (a.width + kTileW - 1) / kTileW;
+    e.n_tiles = e.tiles_x * ((a.height + kTileH - 1) / kTileH);
+    e.counters = nullptr;
+    e.dbg_pixels = nullptr;
+    e.n_dbg = 0;
+    e.dbg_vis = nullptr;
+    return dispatch<false, false>(ex, s, a, e);
+}
+
+int64_t gather_noalloc_max_tiles() { return (int64_t)1 << 30; }
 
 // ==========================================================================
 // diagnostics

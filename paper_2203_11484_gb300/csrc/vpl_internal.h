@@ -121,6 +121,9 @@ struct GatherArgs {
 cudaError_t gbuffer_build(const Exec &ex, const SceneView &s, const CamArgs &c, bool brute,
                           float4 *pos, void *nrm, void *alb, int format);
 cudaError_t gather(const Exec &ex, const SceneView &s, const GatherArgs &a);
+// the same launch with its scratch in static device memory (no allocation)
+cudaError_t gather_noalloc(const Exec &ex, const SceneView &s, const GatherArgs &a);
+int64_t gather_noalloc_max_tiles();
 cudaError_t gather_counters(const Exec &ex, const SceneView &s, const GatherArgs &a,
                             unsigned long long *counters_dev);
 cudaError_t gather_visibility(const Exec &ex, const SceneView &s, const GatherArgs &a,

@@ -94,6 +94,8 @@ _SIGS = {
     "vpl_generate_info": (C.c_int, [_P, C.POINTER(vpl_gen_info)]),
     "vpl_gather": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_gbuffer), C.POINTER(vpl_vpl_set),
                              C.POINTER(vpl_gather_params), _P, _P]),
+    "vpl_gather_noalloc": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_gbuffer), C.POINTER(vpl_vpl_set),
+                                     C.POINTER(vpl_gather_params), _P, _P]),
     "vpl_render": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_camera), C.POINTER(vpl_gen_params),
                              C.POINTER(vpl_gather_params), _P, _P]),
     "vpl_sync": (C.c_int, [_P, _P]),
@@ -309,6 +311,15 @@ def vpl_gather(ctx, scene: int, gbuf: GBuffer, vpls: VplSet, params: W.GatherPar
     gb, vs, p = gbuf.struct(), vpls.struct(), make_gather(params)
     _check(ctx, load().vpl_gather(ctx, scene, C.byref(gb), C.byref(vs), C.byref(p), _ptr(out),
                                   _stream(stream)), "vpl_gather")
+
+
+def vpl_gather_noalloc(ctx, scene: int, gbuf: GBuffer, vpls: VplSet, params: W.GatherParams, out,
+                       stream=None) -> None:
+    """vpl_gather without any device allocation (its scratch is static device
+    memory shared by all calls; see include/vpl.h)."""
+    gb, vs, p = gbuf.struct(), vpls.struct(), make_gather(params)
+    _check(ctx, load().vpl_gather_noalloc(ctx, scene, C.byref(gb), C.byref(vs), C.byref(p), _ptr(out),
+                                          _stream(stream)), "vpl_gather_noalloc")
 
 
 def vpl_render(ctx, scene: int, camera: W.Camera, gen: W.GenParams, params: W.GatherParams, out,
