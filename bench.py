@@ -37,7 +37,7 @@ UNIT = "pairs/s"
 # gather_kernel / warp_occluded / tri_hit (an FMA counts 2)
 FLOPS_PER_PAIR = 28       # d, |d|^2, two cosines, clamp, geometry factor, RGB FMA
 FLOPS_PER_RAY = 15        # segment end points and reciprocal direction
-FLOPS_PER_NODE = 40       # two slab tests per visited node (per active lane)
+FLOPS_PER_NODE = 80       # four slab tests per visited 4-wide node (per active lane)
 FLOPS_PER_TRI = 47        # Moller-Trumbore (per active lane)
 
 

@@ -43,11 +43,17 @@ def _deps_mtime() -> float:
 
 
 def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    """VPL_NVCC_EXTRA (environment) adds nvcc flags, e.g. -DVPL_GATHER_MIN_BLOCKS=7;
+    a change of those flags forces a rebuild."""
     os.makedirs(LIBDIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    tuning = os.environ.get("VPL_NVCC_EXTRA", "").split()
+    stamp = os.path.join(LIBDIR, "flags.txt")
+    old = open(stamp).read() if os.path.exists(stamp) else ""
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime()
+            and old == " ".join(tuning)):
         return LIB
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + tuning
 
     def compile_one(src: str):
         obj = os.path.join(LIBDIR, src.replace(".cu", ".o"))
@@ -69,6 +75,8 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool =
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(" ".join(tuning))
     return LIB
 
 

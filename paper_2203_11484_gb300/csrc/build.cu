@@ -414,30 +414,86 @@ __global__ void bounds_kernel(int n, const int *child, const int *parent_int, co
     }
 }
 
-__global__ void pack_nodes_kernel(int n, const int *child, const float *leafbox, const float *nodebox, float4 *nodes)
+// 4-wide nodes: every binary internal node at even depth becomes one node;
+// its children are its own children where those are leaves, else its
+// grandchildren.  Node index = rank among the even-depth internal nodes in
+// binary order, so the root (binary node 0, depth 0) is node 0.
+__global__ void even_depth_kernel(int n, const int *parent_int, uint32_t *even)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
-    int c0 = child[2 * i], c1 = child[2 * i + 1];
-    const float *a = c0 < 0 ? leafbox + 6 * (int64_t)(~c0) : nodebox + 6 * (int64_t)c0;
-    const float *b = c1 < 0 ? leafbox + 6 * (int64_t)(~c1) : nodebox + 6 * (int64_t)c1;
-    float4 *o = nodes + 4 * (int64_t)i;
-    o[0] = make_float4(a[0], a[3], a[1], a[4]);
-    o[1] = make_float4(b[0], b[3], b[1], b[4]);
-    o[2] = make_float4(a[2], a[5], b[2], b[5]);
-    o[3] = make_float4(__int_as_float(c0), __int_as_float(c1), __int_as_float(1), __int_as_float(1));
+    int d = 0, node = i;
+    while (parent_int[node] >= 0 && d <= 4 * kStackMax) {
+        node = parent_int[node];
+        d++;
+    }
+    even[i] = (d & 1) == 0 ? 1u : 0u;
 }
 
-// one triangle: a root whose first child is the leaf and whose second child
-// is an empty leaf far away
+__device__ __forceinline__ void put_child(float lo[3][4], float hi[3][4], int *ref, int *cnt, int m, int r, int c,
+                                          const float *box)
+{
+    for (int a = 0; a < 3; a++) {
+        lo[a][m] = box[a];
+        hi[a][m] = box[3 + a];
+    }
+    ref[m] = r;
+    cnt[m] = c;
+}
+
+__global__ void pack4_kernel(int n, const int *child, const float *leafbox, const float *nodebox,
+                             const uint32_t *even, const uint32_t *idx4, float4 *nodes)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1 || !even[i]) return;
+    float lo[3][4], hi[3][4];
+    int ref[4], cnt[4], m = 0;
+    for (int j = 0; j < 2; j++) {
+        int c = child[2 * i + j];
+        if (c < 0) {
+            put_child(lo, hi, ref, cnt, m++, c, 1, leafbox + 6 * (int64_t)(~c));
+            continue;
+        }
+        for (int q = 0; q < 2; q++) {
+            int g = child[2 * c + q];
+            if (g < 0) put_child(lo, hi, ref, cnt, m++, g, 1, leafbox + 6 * (int64_t)(~g));
+            else put_child(lo, hi, ref, cnt, m++, (int)idx4[g], 0, nodebox + 6 * (int64_t)g);
+        }
+    }
+    // empty slots: a point box at (3e38, -3e38, 3e38), which no segment or ray
+    // of a scene reaches
+    const float farbox[6] = {3.0e38f, -3.0e38f, 3.0e38f, 3.0e38f, -3.0e38f, 3.0e38f};
+    while (m < 4) put_child(lo, hi, ref, cnt, m++, kEmptyRef, 0, farbox);
+    unsigned leafmask = 0, packed = 0;
+    for (int k = 0; k < 4; k++) {
+        if (ref[k] < 0 && ref[k] != kEmptyRef) leafmask |= 1u << k;
+        packed |= (unsigned)(cnt[k] & 255) << (8 * k);
+    }
+    float4 *o = nodes + 8 * (int64_t)idx4[i];
+    o[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+    o[1] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+    o[2] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+    o[3] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+    o[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+    o[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+    o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
+    o[7] = make_float4(__uint_as_float(leafmask), __uint_as_float(packed), 0.0f, 0.0f);
+}
+
+// one triangle: a root with the leaf in slot 0 and three empty slots
 __global__ void single_root_kernel(const float *leafbox, float4 *nodes)
 {
     const float *a = leafbox;
-    const float far = 3.0e38f;
-    nodes[0] = make_float4(a[0], a[3], a[1], a[4]);
-    nodes[1] = make_float4(far, far, far, far);
-    nodes[2] = make_float4(a[2], a[5], far, far);
-    nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), __int_as_float(1), __int_as_float(0));
+    const float f = 3.0e38f;
+    nodes[0] = make_float4(a[0], f, f, f);
+    nodes[1] = make_float4(a[3], f, f, f);
+    nodes[2] = make_float4(a[1], -f, -f, -f);
+    nodes[3] = make_float4(a[4], -f, -f, -f);
+    nodes[4] = make_float4(a[2], f, f, f);
+    nodes[5] = make_float4(a[5], f, f, f);
+    nodes[6] = make_float4(__int_as_float(~0), __int_as_float(kEmptyRef), __int_as_float(kEmptyRef),
+                           __int_as_float(kEmptyRef));
+    nodes[7] = make_float4(__uint_as_float(1u), __uint_as_float(1u), 0.0f, 0.0f);
 }
 
 __global__ void depth_kernel(int n, const int *parent_int, const int *parent_leaf, int *depth, int *status)
@@ -450,7 +506,7 @@ __global__ void depth_kernel(int n, const int *parent_int, const int *parent_lea
         node = n > 1 ? parent_int[node] : -1;
     }
     atomicMax(depth, d);
-    if (d > kStackMax) latch(status, VPL_ERR_TRAVERSAL_LIMIT);
+    if (d > kDepthMax) latch(status, VPL_ERR_TRAVERSAL_LIMIT);
 }
 
 cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris,
@@ -469,7 +525,7 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
     VPL_TRY(dalloc((void **)&sb->verts, sizeof(float) * 3 * n_verts));
     VPL_TRY(dalloc((void **)&sb->idx, sizeof(int32_t) * 3 * T));
     VPL_TRY(dalloc((void **)&sb->tri, sizeof(float4) * 3 * T));
-    VPL_TRY(dalloc((void **)&sb->nodes, sizeof(float4) * 4 * (T > 1 ? T - 1 : 1)));
+    VPL_TRY(dalloc((void **)&sb->nodes, sizeof(float4) * 8 * (T > 1 ? T - 1 : 1)));
     VPL_TRY(dalloc((void **)&sb->nrm, sizeof(float4) * T));
     VPL_TRY(dalloc((void **)&sb->rho, sizeof(float4) * T));
     VPL_TRY(dalloc((void **)&sb->gbox, sizeof(double) * 6));
@@ -522,8 +578,15 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
                                                            leafbox.as<float>(), nodebox.as<float>(), visits.as<int>(),
                                                            ex.status);
         VPL_LAUNCHED(ex);
-        pack_nodes_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, child.as<int>(), leafbox.as<float>(),
-                                                                   nodebox.as<float>(), sb->nodes);
+        Tmp even, idx4;
+        VPL_TRY(even.alloc(ex, sizeof(uint32_t) * (T - 1)));
+        VPL_TRY(idx4.alloc(ex, sizeof(uint32_t) * T));
+        even_depth_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, pint.as<int>(), even.as<uint32_t>());
+        VPL_LAUNCHED(ex);
+        VPL_TRY(exclusive_scan<uint32_t>(ex, even.as<uint32_t>(), idx4.as<uint32_t>(), nullptr, T - 1));
+        pack4_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, child.as<int>(), leafbox.as<float>(),
+                                                              nodebox.as<float>(), even.as<uint32_t>(),
+                                                              idx4.as<uint32_t>(), sb->nodes);
         VPL_LAUNCHED(ex);
     }
     depth_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(n, pint.as<int>(), pleaf.as<int>(), sb->depth, ex.status);

@@ -17,6 +17,11 @@ namespace vpl {
 
 constexpr int kGatherWarps = 4;
 constexpr int kTileW = 8, kTileH = 4;
+// resident blocks per SM the gather is compiled for (register budget
+// 65536 / (128 * blocks)); a build-time tuning knob
+#ifndef VPL_GATHER_MIN_BLOCKS
+#define VPL_GATHER_MIN_BLOCKS 5
+#endif
 
 __device__ __forceinline__ float4 load_attr(const void *base, int64_t i, int fmt)
 {
@@ -95,9 +100,10 @@ struct GatherExtra {
 };
 
 template <int VIS, int PREC, bool COUNT, bool DEBUG>
-__global__ void __launch_bounds__(kGatherWarps * 32) gather_kernel(SceneView s, GatherArgs a, GatherExtra e, int *status)
+__global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gather_kernel(SceneView s, GatherArgs a, GatherExtra e, int *status)
 {
     __shared__ float4 stage[kGatherWarps][3][32];
+    __shared__ int stack[kGatherWarps][kStackMax]; // per-warp traversal stacks
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gfmt = PREC == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     const int M = a.count;
@@ -126,6 +132,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) gather_kernel(SceneView s, 
         float4 gn = valid ? load_attr(a.g_nrm, p, gfmt) : make_float4(0, 0, 0, 0);
         const float3 y = f3(gp), ny = f3(gn);
         const float3 o = y + ny * eps;
+        int occ_cache = -1;                    // last blocking triangle of this pixel
         float ax = 0.0f, ay = 0.0f, az = 0.0f; // running sums
         float cx = 0.0f, cy_ = 0.0f, cz = 0.0f; // Kahan compensation
         for (int base = 0; base < M; base += 32) {
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) gather_kernel(SceneView s, 
                 bool vis = true;
                 if (VIS == VPL_VIS_BVH) {
                     const float3 q = f3(xp) + f3(xn) * eps;
-                    vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), status, wc);
+                    vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), occ_cache, stack[wid], status, wc);
                 } else if (VIS == VPL_VIS_BRUTE) {
                     const float3 q = f3(xp) + f3(xn) * eps;
                     vis = !warp_occluded_brute<COUNT>(s, want, make_ray(o, q - o), wc);

@@ -13,7 +13,8 @@
 namespace vpl {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kStackMax = 96;            // BVH depth is checked against this at build time
+constexpr int kDepthMax = 96;            // binary LBVH depth, checked when a scene is built
+constexpr int kStackMax = 160;           // >= 3 x depth of the 4-wide tree, (kDepthMax + 1) / 2 + 1
 constexpr int kTraversalLimit = 1 << 16; // node visits per query before giving up
 constexpr float kPi = 3.14159265358979323846f;
 constexpr double kPiD = 3.14159265358979323846;
@@ -189,89 +190,124 @@ __device__ __forceinline__ bool tri_hit(const Ray &r, float4 v0, float4 e1v, flo
     return true;
 }
 
-// slab test of both children of a node against [tlo, thi]
-// node layout: n0 = (c0 lo.x, c0 hi.x, c0 lo.y, c0 hi.y), n1 = same for c1,
-//              n2 = (c0 lo.z, c0 hi.z, c1 lo.z, c1 hi.z),
-//              n3 = (child0, child1, leaf count0, leaf count1) as int bits
-__device__ __forceinline__ void slab2(const Ray &r, float4 n0, float4 n1, float4 n2, float tlo,
-                                      float thi, bool &h0, bool &h1, float &te0, float &te1)
+// --------------------------------------------------------------------------
+// 4-wide BVH nodes (8 float4 = 128 B): lo.x / hi.x / lo.y / hi.y / lo.z / hi.z
+// of the four children, their references (>= 0 node, < 0 leaf ~first
+// triangle slot, kEmptyRef none) and the triangle count of leaf children.
+// --------------------------------------------------------------------------
+constexpr int kEmptyRef = (int)0x80000000;
+
+struct Node4 {
+    float4 lx, hx, ly, hy, lz, hz;
+    int ref[4], cnt[4];
+    unsigned leafmask; // bit k set: child k is a leaf
+};
+
+__device__ __forceinline__ void load_node4(const float4 *nodes, int node, Node4 &n)
 {
-    float ax = fmaf(n0.x, r.inv.x, -r.oinv.x), bx = fmaf(n0.y, r.inv.x, -r.oinv.x);
-    float ay = fmaf(n0.z, r.inv.y, -r.oinv.y), by = fmaf(n0.w, r.inv.y, -r.oinv.y);
-    float az = fmaf(n2.x, r.inv.z, -r.oinv.z), bz = fmaf(n2.y, r.inv.z, -r.oinv.z);
-    float lo0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), tlo));
-    float hi0 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), thi));
-    float cx = fmaf(n1.x, r.inv.x, -r.oinv.x), dx = fmaf(n1.y, r.inv.x, -r.oinv.x);
-    float cy = fmaf(n1.z, r.inv.y, -r.oinv.y), dy = fmaf(n1.w, r.inv.y, -r.oinv.y);
-    float cz = fmaf(n2.z, r.inv.z, -r.oinv.z), dz = fmaf(n2.w, r.inv.z, -r.oinv.z);
-    float lo1 = fmaxf(fmaxf(fminf(cx, dx), fminf(cy, dy)), fmaxf(fminf(cz, dz), tlo));
-    float hi1 = fminf(fminf(fmaxf(cx, dx), fmaxf(cy, dy)), fminf(fmaxf(cz, dz), thi));
-    h0 = lo0 <= hi0;
-    h1 = lo1 <= hi1;
-    te0 = lo0;
-    te1 = lo1;
+    const float4 *p = nodes + 8 * (int64_t)node;
+    n.lx = __ldg(p);
+    n.hx = __ldg(p + 1);
+    n.ly = __ldg(p + 2);
+    n.hy = __ldg(p + 3);
+    n.lz = __ldg(p + 4);
+    n.hz = __ldg(p + 5);
+    float4 r = __ldg(p + 6), c = __ldg(p + 7);
+    n.ref[0] = __float_as_int(r.x); n.ref[1] = __float_as_int(r.y);
+    n.ref[2] = __float_as_int(r.z); n.ref[3] = __float_as_int(r.w);
+    n.leafmask = __float_as_uint(c.x);
+    const unsigned packed = __float_as_uint(c.y); // 8-bit triangle counts of leaf children
+    n.cnt[0] = packed & 255u; n.cnt[1] = (packed >> 8) & 255u;
+    n.cnt[2] = (packed >> 16) & 255u; n.cnt[3] = packed >> 24;
 }
 
-__device__ __forceinline__ void load_node(const float4 *nodes, int node, float4 &n0, float4 &n1,
-                                          float4 &n2, float4 &n3)
+__device__ __forceinline__ float fmin3(float a, float b, float c)
 {
-    const float4 *p = nodes + 4 * (int64_t)node;
-    n0 = __ldg(p);
-    n1 = __ldg(p + 1);
-    n2 = __ldg(p + 2);
-    n3 = __ldg(p + 3);
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float comp(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
+// slab test of child k of a node against [tlo, thi]; te = entry parameter
+__device__ __forceinline__ bool slab(const Ray &r, const Node4 &n, int k, float tlo, float thi, float &te)
+{
+    float ax = fmaf(comp(n.lx, k), r.inv.x, -r.oinv.x), bx = fmaf(comp(n.hx, k), r.inv.x, -r.oinv.x);
+    float ay = fmaf(comp(n.ly, k), r.inv.y, -r.oinv.y), by = fmaf(comp(n.hy, k), r.inv.y, -r.oinv.y);
+    float az = fmaf(comp(n.lz, k), r.inv.z, -r.oinv.z), bz = fmaf(comp(n.hz, k), r.inv.z, -r.oinv.z);
+    float lo = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), tlo));
+    float hi = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fminf(fmaxf(az, bz), thi));
+    te = lo;
+    return lo <= hi;
+}
+
+__device__ __forceinline__ void cswap(float &ta, int &ra, float &tb, int &rb)
+{
+    if (tb < ta) {
+        float t = ta; ta = tb; tb = t;
+        int q = ra; ra = rb; rb = q;
+    }
 }
 
 // closest hit with t in (tmin, inf); ties to the lower original triangle id.
 // Returns the original triangle id or -1.
 static __device__ __noinline__ int closest_hit(const SceneView &s, const Ray &r, float tmin, float &tbest,
-                                        int *status)
+                                               int *status)
 {
     int stack[kStackMax];
     int sp = 0, node = 0, best = -1, steps = 0;
-    tbest = __int_as_float(0x7f800000);
+    const float kInf = __int_as_float(0x7f800000);
+    tbest = kInf;
     while (true) {
-        float4 n0, n1, n2, n3;
-        load_node(s.nodes, node, n0, n1, n2, n3);
-        bool h0, h1;
-        float t0, t1;
-        slab2(r, n0, n1, n2, tmin, tbest, h0, h1, t0, t1);
-        int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-        if (h0 && c0 < 0) {
-            int first = ~c0, cnt = __float_as_int(n3.z);
-            for (int k = first; k < first + cnt; k++) {
-                float4 v0 = __ldg(s.tri + 3 * k), e1 = __ldg(s.tri + 3 * k + 1), e2 = __ldg(s.tri + 3 * k + 2);
-                float t;
-                int id = __float_as_int(v0.w);
-                if (tri_hit(r, v0, e1, e2, t) && t > tmin && (t < tbest || (t == tbest && id < best))) {
-                    tbest = t;
-                    best = id;
+        Node4 n;
+        load_node4(s.nodes, node, n);
+        float te[4];
+        int rf[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            rf[k] = n.ref[k];
+            bool h = rf[k] != kEmptyRef && slab(r, n, k, tmin, tbest, te[k]);
+            if (h && rf[k] < 0) {
+                for (int q = ~rf[k]; q < ~rf[k] + n.cnt[k]; q++) {
+                    float4 v0 = __ldg(s.tri + 3 * q);
+                    float t;
+                    int id = __float_as_int(v0.w);
+                    if (tri_hit(r, v0, __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2), t) && t > tmin &&
+                        (t < tbest || (t == tbest && id < best))) {
+                        tbest = t;
+                        best = id;
+                    }
                 }
+                h = false;
             }
-            h0 = false;
-        }
-        if (h1 && c1 < 0) {
-            int first = ~c1, cnt = __float_as_int(n3.w);
-            for (int k = first; k < first + cnt; k++) {
-                float4 v0 = __ldg(s.tri + 3 * k), e1 = __ldg(s.tri + 3 * k + 1), e2 = __ldg(s.tri + 3 * k + 2);
-                float t;
-                int id = __float_as_int(v0.w);
-                if (tri_hit(r, v0, e1, e2, t) && t > tmin && (t < tbest || (t == tbest && id < best))) {
-                    tbest = t;
-                    best = id;
-                }
+            if (!h) {          // only internal children that the ray enters stay
+                te[k] = kInf;
+                rf[k] = kEmptyRef;
             }
-            h1 = false;
         }
-        if (h0 && h1) {
-            int nearc = t0 <= t1 ? c0 : c1, farc = t0 <= t1 ? c1 : c0;
-            if (sp >= kStackMax) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
-            stack[sp++] = farc;
-            node = nearc;
-        } else if (h0) {
-            node = c0;
-        } else if (h1) {
-            node = c1;
+        // nearest internal child next, the others pushed farthest first
+        cswap(te[0], rf[0], te[1], rf[1]);
+        cswap(te[2], rf[2], te[3], rf[3]);
+        cswap(te[0], rf[0], te[2], rf[2]);
+        cswap(te[1], rf[1], te[3], rf[3]);
+        cswap(te[1], rf[1], te[2], rf[2]);
+        bool overflow = false;
+#pragma unroll
+        for (int k = 3; k >= 1; k--)
+            if (rf[k] != kEmptyRef && te[k] <= tbest) {
+                if (sp >= kStackMax) overflow = true;
+                else stack[sp++] = rf[k];
+            }
+        if (overflow) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
+        if (rf[0] != kEmptyRef && te[0] <= tbest) {
+            node = rf[0];
         } else {
             if (sp == 0) break;
             node = stack[--sp];
@@ -287,40 +323,30 @@ static __device__ __noinline__ bool occluded1(const SceneView &s, const Ray &r, 
     int stack[kStackMax];
     int sp = 0, node = 0, steps = 0;
     while (true) {
-        float4 n0, n1, n2, n3;
-        load_node(s.nodes, node, n0, n1, n2, n3);
-        bool h0, h1;
-        float t0, t1;
-        slab2(r, n0, n1, n2, 0.0f, 1.0f, h0, h1, t0, t1);
-        int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-        if (h0 && c0 < 0) {
-            int first = ~c0, cnt = __float_as_int(n3.z);
-            for (int k = first; k < first + cnt; k++) {
-                float t;
-                if (tri_hit(r, __ldg(s.tri + 3 * k), __ldg(s.tri + 3 * k + 1), __ldg(s.tri + 3 * k + 2), t) &&
-                    t > 0.0f && t < 1.0f)
-                    return true;
+        Node4 n;
+        load_node4(s.nodes, node, n);
+        int next = -1;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            float te;
+            int rf = n.ref[k];
+            if (rf == kEmptyRef || !slab(r, n, k, 0.0f, 1.0f, te)) continue;
+            if (rf < 0) {
+                for (int q = ~rf; q < ~rf + n.cnt[k]; q++) {
+                    float t;
+                    if (tri_hit(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2), t) &&
+                        t > 0.0f && t < 1.0f)
+                        return true;
+                }
+            } else if (next < 0) {
+                next = rf;
+            } else {
+                if (sp >= kStackMax) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); return false; }
+                stack[sp++] = rf;
             }
-            h0 = false;
         }
-        if (h1 && c1 < 0) {
-            int first = ~c1, cnt = __float_as_int(n3.w);
-            for (int k = first; k < first + cnt; k++) {
-                float t;
-                if (tri_hit(r, __ldg(s.tri + 3 * k), __ldg(s.tri + 3 * k + 1), __ldg(s.tri + 3 * k + 2), t) &&
-                    t > 0.0f && t < 1.0f)
-                    return true;
-            }
-            h1 = false;
-        }
-        if (h0 && h1) {
-            if (sp >= kStackMax) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); return false; }
-            stack[sp++] = t0 <= t1 ? c1 : c0;
-            node = t0 <= t1 ? c0 : c1;
-        } else if (h0) {
-            node = c0;
-        } else if (h1) {
-            node = c1;
+        if (next >= 0) {
+            node = next;
         } else {
             if (sp == 0) return false;
             node = stack[--sp];
@@ -360,11 +386,13 @@ __device__ __forceinline__ bool occluded_brute(const SceneView &s, const Ray &r)
 
 // --------------------------------------------------------------------------
 // warp-wide packet traversal for shadow segments.  All 32 lanes call it
-// together; lanes with want == false ride along.  The traversal stack is
-// warp-uniform and lives in registers spread over the lanes (entry e in
-// lane e % 32, slot e / 32), so pushes are a predicated move and pops a
-// shuffle.  Node and triangle loads are the same address in every lane
-// (one transaction, broadcast).
+// together; lanes with want == false ride along.  Node and triangle loads are
+// the same address in every lane (one transaction, broadcast).  Per node each
+// lane forms a 4-bit mask of the children its segment enters; one OR-reduction
+// over the warp gives the children any lane needs.  Leaf children are tested
+// at once; among internal children the packet descends into the one the first
+// live lane enters first and pushes the others on a warp-uniform stack in
+// shared memory (`stk`, kStackMax entries per warp).
 // --------------------------------------------------------------------------
 struct WarpCounters {
     uint32_t visits, tests; // per lane: nodes visited / triangles tested by its own ray
@@ -373,76 +401,100 @@ struct WarpCounters {
 
 template <bool COUNT>
 __device__ __forceinline__ void leaf_any(const SceneView &s, const Ray &r, int first, int cnt,
-                                         bool mask, bool &occl, WarpCounters &wc)
+                                         bool mask, bool &occl, int &cache, WarpCounters &wc)
 {
     for (int k = first; k < first + cnt; k++) {
         float4 v0 = __ldg(s.tri + 3 * k), e1 = __ldg(s.tri + 3 * k + 1), e2 = __ldg(s.tri + 3 * k + 2);
         if (mask && !occl) {
             float t;
             if (COUNT) wc.tests++;
-            if (tri_hit(r, v0, e1, e2, t) && t > 0.0f && t < 1.0f) occl = true;
+            if (tri_hit(r, v0, e1, e2, t) && t > 0.0f && t < 1.0f) {
+                occl = true;
+                cache = k;
+            }
         }
     }
 }
 
+// `cache` (per lane) is the leaf-order slot of the triangle that last blocked
+// one of this lane's segments, or -1.  It is tested before the traversal:
+// neighbouring VPLs are usually hidden by the same triangle.  The answer is
+// the same with or without it (a segment is blocked when any triangle blocks
+// it).
 template <bool COUNT>
-__device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, const Ray &r, int *status,
-                                              WarpCounters &wc)
+__device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, const Ray &r, int &cache,
+                                              int *stk, int *status, WarpCounters &wc)
 {
     const int lane = threadIdx.x & 31;
     bool occl = false;
-    if (__ballot_sync(kFull, want) == 0) return false;
-    int slot0 = 0, slot1 = 0, slot2 = 0; // stack entries held by this lane
+    if (want && cache >= 0) {
+        float t;
+        if (COUNT) wc.tests++;
+        if (tri_hit(r, __ldg(s.tri + 3 * cache), __ldg(s.tri + 3 * cache + 1), __ldg(s.tri + 3 * cache + 2), t) &&
+            t > 0.0f && t < 1.0f)
+            occl = true;
+    }
+    unsigned alive = __ballot_sync(kFull, want && !occl);
+    if (alive == 0) return occl;
     int sp = 0, node = 0, steps = 0;
+    const float kInf = __int_as_float(0x7f800000);
     while (true) {
-        float4 n0, n1, n2, n3;
-        load_node(s.nodes, node, n0, n1, n2, n3);
-        bool live = want && !occl;
-        bool h0, h1;
-        float t0, t1;
-        slab2(r, n0, n1, n2, 0.0f, 1.0f, h0, h1, t0, t1);
-        h0 = h0 && live;
-        h1 = h1 && live;
+        Node4 n;
+        load_node4(s.nodes, node, n);
+        const bool live = want && !occl;
+        const unsigned leafmask = n.leafmask;
+        unsigned hits = 0;     // children this lane's segment enters
+        int mine = -1;         // the nearest internal one
+        float tmine = kInf;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            float te;
+            // empty slots hold a box no segment of a scene reaches: no test needed
+            if (live && slab(r, n, k, 0.0f, 1.0f, te)) {
+                hits |= 1u << k;
+                if (!((leafmask >> k) & 1u) && te < tmine) {
+                    tmine = te;
+                    mine = k;
+                }
+            }
+        }
         if (COUNT) {
             wc.steps++;
             if (live) wc.visits++;
         }
-        int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-        if (c0 < 0) {
-            if (__any_sync(kFull, h0)) leaf_any<COUNT>(s, r, ~c0, __float_as_int(n3.z), h0, occl, wc);
-            h0 = false;
+        unsigned any = __reduce_or_sync(kFull, hits);
+        if (any & leafmask) {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if ((any & leafmask) >> k & 1u)
+                    leaf_any<COUNT>(s, r, ~n.ref[k], n.cnt[k], (hits >> k) & 1u, occl, cache, wc);
+            alive = __ballot_sync(kFull, want && !occl);
+            if (alive == 0) break;
+            any = __reduce_or_sync(kFull, occl ? 0u : hits);
         }
-        if (c1 < 0) {
-            if (__any_sync(kFull, h1)) leaf_any<COUNT>(s, r, ~c1, __float_as_int(n3.w), h1, occl, wc);
-            h1 = false;
-        }
-        h0 = h0 && !occl;
-        h1 = h1 && !occl;
-        unsigned b0 = __ballot_sync(kFull, h0), b1 = __ballot_sync(kFull, h1);
-        if (b0 && b1) {
-            // visit first the child that most of the lanes needing both enter first
-            unsigned both = b0 & b1;
-            unsigned near0 = __ballot_sync(kFull, h0 && h1 && t0 <= t1);
-            bool first0 = 2 * __popc(near0) >= __popc(both);
-            int nearc = first0 ? c0 : c1, farc = first0 ? c1 : c0;
-            if (sp >= kStackMax) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
-            if (lane == (sp & 31)) {
-                if (sp < 32) slot0 = farc; else if (sp < 64) slot1 = farc; else slot2 = farc;
+        unsigned need = any & ~leafmask;
+        if (need) {
+            // descend where the first live lane goes first (else the lowest child needed)
+            const int leader = __ffs(__ballot_sync(kFull, want && !occl)) - 1;
+            int pick = __shfl_sync(kFull, occl ? -1 : mine, leader);
+            if (pick < 0) pick = __ffs(need) - 1;
+            need &= ~(1u << pick);
+            if (sp + __popc(need) > kStackMax) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
+            while (need) {
+                int k = __ffs(need) - 1;
+                need &= need - 1;
+                if (lane == 0) stk[sp] = k == 0 ? n.ref[0] : k == 1 ? n.ref[1] : k == 2 ? n.ref[2] : n.ref[3];
+                sp++;
             }
-            sp++;
-            node = nearc;
-        } else if (b0) {
-            node = c0;
-        } else if (b1) {
-            node = c1;
+            node = pick == 0 ? n.ref[0] : pick == 1 ? n.ref[1] : pick == 2 ? n.ref[2] : n.ref[3];
         } else {
-            if (sp == 0 || __ballot_sync(kFull, want && !occl) == 0) break;
-            sp--;
-            int v = sp < 32 ? slot0 : (sp < 64 ? slot1 : slot2);
-            node = __shfl_sync(kFull, v, sp & 31);
+            if (sp == 0) break;
+            __syncwarp();
+            node = stk[--sp];
         }
         if (++steps > kTraversalLimit) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
     }
+    __syncwarp();
     return occl;
 }
 
