@@ -196,8 +196,15 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     B.build_library()
 
-    wl = W.room200k_workload(width=args.width, height=args.height, m_total=args.vpls,
-                             seed=1 + rank)  # each rank renders its own close-up view
+    prec = {"fp32": W.PREC_FP32, "fp16_kahan": W.PREC_FP16_KAHAN, "fp16_plain": W.PREC_FP16_PLAIN}[args.precision]
+    fmt = V.FORMAT_FP32 if prec == W.PREC_FP32 else V.FORMAT_FP16
+    # each rank renders its own close-up view
+    if args.workload == "clutter1m":
+        wl = W.room1m_workload(width=args.width or 1920, height=args.height or 1080, m_total=args.vpls or 32768,
+                               precision=prec, seed=4 + rank)
+    else:
+        wl = W.room200k_workload(width=args.width or 1024, height=args.height or 1024,
+                                 m_total=args.vpls or 4096, precision=prec, seed=1 + rank)
     view = wl.views[0]
     cam, gen, gat = view.camera, view.gen, view.gather
     M = gen.m_close + gen.m_far
@@ -212,8 +219,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     ctx = V.Context(dev)
-    gb = V.GBuffer.empty(cam.width, cam.height)
-    vs = V.VplSet.empty(M)
+    gb = V.GBuffer.empty(cam.width, cam.height, fmt=fmt)
+    vs = V.VplSet.empty(M, fmt=fmt)
 
     def step(o, gev=None):
         """Whole hot path through the C ABI: upload + BVH, G-buffer, VPLs, gather."""
@@ -294,7 +301,7 @@ def run_ours(args):
     achieved = flops / (gather_in_step_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "gather_kernel<BVH,FP32>",
+                "kernel": f"gather_kernel<BVH,{args.precision}>",
                 "peak_note": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz",
                 "counters": {"pairs": cnt[0], "shadow_rays": cnt[1], "node_visits": cnt[2],
                              "tri_tests": cnt[3], "blocked": cnt[4], "warp_steps": cnt[5],
@@ -342,7 +349,8 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if prec == W.PREC_FP32 else "f16 attributes, f32 shading", "data": "synthetic",
                 "config": {"workload": wl.name, "width": cam.width, "height": cam.height, "vpls": M,
                            "m_close": gen.m_close, "m_far": gen.m_far, "tris": sc.n_tris,
                            "visibility": "bvh", "parallelism": f"replicas x{ws}",
@@ -369,9 +377,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--width", type=int, default=1024)
-    ap.add_argument("--height", type=int, default=1024)
-    ap.add_argument("--vpls", type=int, default=4096)
+    ap.add_argument("--workload", default="room200k", choices=["room200k", "clutter1m"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16_kahan", "fp16_plain"])
+    ap.add_argument("--width", type=int, default=0, help="0: the workload's size")
+    ap.add_argument("--height", type=int, default=0)
+    ap.add_argument("--vpls", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

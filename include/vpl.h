@@ -37,11 +37,15 @@
  *    nrm[p]    float4 (unit geometric normal, 0)      | half4 in FP16 format
  *    albedo[p] float4 (r, g, b, 0)                    | half4 in FP16 format
  *  VPL row i (patch VPLs first in stratum order, then distant VPLs in
- *  (path, bounce) order):
+ *  (path, bounce) order), FP32 format:
  *    pos[i]    float4 (x, y, z, triangle id as int bits)
- *    nrm[i]    float4 (unit normal, tag as int bits)  | half4 in FP16 format
+ *    nrm[i]    float4 (unit normal, tag as int bits)
  *              tag = stratum k for patch VPLs, 16 * path + bounce otherwise
- *    flux[i]   float4 (reflected power r, g, b, 0)    | half4 in FP16 format
+ *    flux[i]   float4 (reflected power r, g, b, 0)
+ *  FP16 format (32 bytes a row):
+ *    pos[i]    float4 (x, y, z, m) with m = max(r, g, b) in FP32
+ *    nrm[i]    half4 (unit normal, 0)
+ *    flux[i]   half4 (r / m, g / m, b / m, 0): colour in FP16, magnitude in FP32
  *  Image: float4 (r, g, b, 0) per pixel, same row order as the G-buffer.
  */
 #ifndef VPL_H

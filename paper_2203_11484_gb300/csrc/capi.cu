@@ -222,8 +222,6 @@ int check_gather(vpl_ctx *ctx, const vpl_gather_params *p, int gfmt, int vfmt)
     int want = p->precision == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     if (gfmt != want || vfmt != want)
         return fail(ctx, VPL_ERR_INVALID_ARG, "buffer formats must be FP32 for precision 0 and FP16 otherwise");
-    if (p->precision != VPL_PREC_FP32)
-        return fail(ctx, VPL_ERR_UNSUPPORTED, "FP16-attribute gather is not built into this library");
     return VPL_OK;
 }
 
@@ -451,8 +449,6 @@ int vpl_generate(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const 
     if ((rc = check_vpls(ctx, vpls))) return rc;
     if (vpls->count != gen->m_close + gen->m_far)
         return fail(ctx, VPL_ERR_INVALID_ARG, "vpl set count must equal m_close + m_far");
-    if (vpls->format != VPL_FORMAT_FP32)
-        return fail(ctx, VPL_ERR_UNSUPPORTED, "vpl_generate writes FP32 VPL sets");
     DeviceGuard g(ctx->device);
     Exec ex = exec_of(ctx, stream);
     CK(ctx, generate_vpls(ex, view_of(s), gen_args(F, gen, s->light), (float4 *)vpls->pos, vpls->nrm, vpls->flux,
@@ -531,28 +527,30 @@ int vpl_render(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const vp
     int rc = camera_frame(ctx, cam, &F);
     if (rc) return rc;
     if ((rc = check_gen(ctx, gen))) return rc;
-    if ((rc = check_gather(ctx, params, VPL_FORMAT_FP32, VPL_FORMAT_FP32))) return rc;
+    const int fmt = params && params->precision != VPL_PREC_FP32 ? VPL_FORMAT_FP16 : VPL_FORMAT_FP32;
+    if ((rc = check_gather(ctx, params, fmt, fmt))) return rc;
     const int64_t npx = (int64_t)cam->width * cam->height;
     if (npx > 0 && !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "out_rgba is NULL");
     DeviceGuard g(ctx->device);
     Exec ex = exec_of(ctx, stream);
     const int64_t M = (int64_t)gen->m_close + gen->m_far;
     Tmp gpos, gnrm, galb, vpos, vnrm, vflux;
+    const size_t attr = fmt == VPL_FORMAT_FP16 ? 8 : 16; // half4 or float4 rows
     CK(ctx, gpos.alloc(ex, sizeof(float4) * npx), "vpl_render");
-    CK(ctx, gnrm.alloc(ex, sizeof(float4) * npx), "vpl_render");
-    CK(ctx, galb.alloc(ex, sizeof(float4) * npx), "vpl_render");
+    CK(ctx, gnrm.alloc(ex, attr * npx), "vpl_render");
+    CK(ctx, galb.alloc(ex, attr * npx), "vpl_render");
     CK(ctx, vpos.alloc(ex, sizeof(float4) * M), "vpl_render");
-    CK(ctx, vnrm.alloc(ex, sizeof(float4) * M), "vpl_render");
-    CK(ctx, vflux.alloc(ex, sizeof(float4) * M), "vpl_render");
-    vpl_gbuffer gb = {gpos.p, gnrm.p, galb.p, cam->width, cam->height, VPL_FORMAT_FP32, 0};
-    vpl_vpl_set vs = {vpos.p, vnrm.p, vflux.p, (int32_t)M, VPL_FORMAT_FP32};
+    CK(ctx, vnrm.alloc(ex, attr * M), "vpl_render");
+    CK(ctx, vflux.alloc(ex, attr * M), "vpl_render");
+    vpl_gbuffer gb = {gpos.p, gnrm.p, galb.p, cam->width, cam->height, fmt, 0};
+    vpl_vpl_set vs = {vpos.p, vnrm.p, vflux.p, (int32_t)M, fmt};
     SceneView v = view_of(s);
     mark(ctx, 2, stream);
     CK(ctx, gbuffer_build(ex, v, cam_args(F, cam), params->visibility == VPL_VIS_BRUTE, gpos.as<float4>(), gnrm.p,
-                          galb.p, VPL_FORMAT_FP32),
+                          galb.p, fmt),
        "vpl_render gbuffer");
     mark(ctx, 3, stream);
-    CK(ctx, generate_vpls(ex, v, gen_args(F, gen, s->light), vpos.as<float4>(), vnrm.p, vflux.p, VPL_FORMAT_FP32,
+    CK(ctx, generate_vpls(ex, v, gen_args(F, gen, s->light), vpos.as<float4>(), vnrm.p, vflux.p, fmt,
                           ctx->d_info),
        "vpl_render generate");
     mark(ctx, 4, stream);

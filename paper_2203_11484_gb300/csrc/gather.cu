@@ -141,9 +141,16 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
             if (__shfl_sync(kFull, st, 0) != 0) break;
             const int i = base + lane;
             if (i < M) {
-                stage[wid][0][lane] = __ldg(a.v_pos + i);
+                const float4 vp = __ldg(a.v_pos + i);
+                float4 vf = load_attr(a.v_flux, i, gfmt);
+                if (gfmt == VPL_FORMAT_FP16) { // FP16 colour x FP32 magnitude (pos.w)
+                    vf.x *= vp.w;
+                    vf.y *= vp.w;
+                    vf.z *= vp.w;
+                }
+                stage[wid][0][lane] = vp;
                 stage[wid][1][lane] = load_attr(a.v_nrm, i, gfmt);
-                stage[wid][2][lane] = load_attr(a.v_flux, i, gfmt);
+                stage[wid][2][lane] = vf;
             }
             __syncwarp();
             const int cnt = min(32, M - base);
@@ -228,6 +235,12 @@ static cudaError_t dispatch(const Exec &ex, const SceneView &s, const GatherArgs
     VPL_CASE(VPL_VIS_BVH, VPL_PREC_FP32)
     VPL_CASE(VPL_VIS_BRUTE, VPL_PREC_FP32)
     VPL_CASE(VPL_VIS_NONE, VPL_PREC_FP32)
+    VPL_CASE(VPL_VIS_BVH, VPL_PREC_FP16_KAHAN)
+    VPL_CASE(VPL_VIS_BVH, VPL_PREC_FP16_PLAIN)
+    VPL_CASE(VPL_VIS_BRUTE, VPL_PREC_FP16_KAHAN)
+    VPL_CASE(VPL_VIS_BRUTE, VPL_PREC_FP16_PLAIN)
+    VPL_CASE(VPL_VIS_NONE, VPL_PREC_FP16_KAHAN)
+    VPL_CASE(VPL_VIS_NONE, VPL_PREC_FP16_PLAIN)
 #undef VPL_CASE
     return cudaErrorInvalidValue;
 }

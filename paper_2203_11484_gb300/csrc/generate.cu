@@ -116,14 +116,27 @@ __device__ __forceinline__ uint64_t stratum_point(uint64_t a, uint64_t F, uint64
     return (d1 << 32) + d0;
 }
 
-__device__ __forceinline__ void store_attr(void *base, int64_t i, float4 v, int fmt)
+// One VPL row.  FP32 format: pos (x, y, z, triangle), nrm (n, tag), flux
+// (r, g, b, 0).  FP16 format: pos (x, y, z, m) with m = max(r, g, b) in FP32,
+// nrm half4 (n, 0), flux half4 (r/m, g/m, b/m, 0): FP16 holds the colour, FP32
+// the magnitude, so fluxes of any size keep an 11-bit mantissa.
+__device__ __forceinline__ void store_vpl(float4 *pos, void *nrm, void *flux, int64_t i, float3 x, int tri,
+                                          float3 n, int tag, float3 phi, int fmt)
 {
     if (fmt == VPL_FORMAT_FP16) {
-        __half2 *p = reinterpret_cast<__half2 *>(base) + 2 * i;
-        p[0] = __floats2half2_rn(v.x, v.y);
-        p[1] = __floats2half2_rn(v.z, 0.0f);
+        const float m = fmaxf(phi.x, fmaxf(phi.y, phi.z));
+        const float inv = m > 0.0f ? 1.0f / m : 0.0f;
+        pos[i] = make_float4(x.x, x.y, x.z, m);
+        __half2 *pn = reinterpret_cast<__half2 *>(nrm) + 2 * i;
+        pn[0] = __floats2half2_rn(n.x, n.y);
+        pn[1] = __floats2half2_rn(n.z, 0.0f);
+        __half2 *pf = reinterpret_cast<__half2 *>(flux) + 2 * i;
+        pf[0] = __floats2half2_rn(phi.x * inv, phi.y * inv);
+        pf[1] = __floats2half2_rn(phi.z * inv, 0.0f);
     } else {
-        reinterpret_cast<float4 *>(base)[i] = v;
+        pos[i] = make_float4(x.x, x.y, x.z, __int_as_float(tri));
+        reinterpret_cast<float4 *>(nrm)[i] = make_float4(n.x, n.y, n.z, __int_as_float(tag));
+        reinterpret_cast<float4 *>(flux)[i] = make_float4(phi.x, phi.y, phi.z, 0.0f);
     }
 }
 
@@ -147,15 +160,14 @@ __device__ __forceinline__ bool seg_blocked(const SceneView &s, D3 p, D3 q, int 
 // (2): one thread per stratum k
 __global__ void patch_kernel(SceneView s, GenArgs g, const uint32_t *sorted, const unsigned long long *F,
                              const int *n_close, const GenInfoDev *info, float4 *pos, void *nrm, void *flux,
-                             int fmt, float flux_scale, int *status)
+                             int fmt, int *status)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.m_close) return;
     const int nc = *n_close;
     if (nc == 0) {
-        pos[k] = make_float4(0, 0, 0, __int_as_float(-1));
-        store_attr(nrm, k, make_float4(0, 0, 0, __int_as_float(k)), fmt);
-        store_attr(flux, k, make_float4(0, 0, 0, 0), fmt);
+        const float3 z = make_float3(0.0f, 0.0f, 0.0f);
+        store_vpl(pos, nrm, flux, k, z, -1, z, k, z, fmt);
         if (k == 0) latch(status, VPL_ERR_EMPTY_CLOSE);
         return;
     }
@@ -205,13 +217,11 @@ __global__ void patch_kernel(SceneView s, GenArgs g, const uint32_t *sorted, con
         acc = D * acc / (double)g.light_samples;
     }
     float4 rho = __ldg(s.rho + t);
-    pos[k] = make_float4((float)x.x, (float)x.y, (float)x.z, __int_as_float(t));
-    store_attr(nrm, k, make_float4((float)n.x, (float)n.y, (float)n.z, __int_as_float(k)), fmt);
-    store_attr(flux, k,
-               make_float4((float)((double)rho.x * L.power[0] * acc * flux_scale),
-                           (float)((double)rho.y * L.power[1] * acc * flux_scale),
-                           (float)((double)rho.z * L.power[2] * acc * flux_scale), 0.0f),
-               fmt);
+    store_vpl(pos, nrm, flux, k, make_float3((float)x.x, (float)x.y, (float)x.z), t,
+              make_float3((float)n.x, (float)n.y, (float)n.z), k,
+              make_float3((float)((double)rho.x * L.power[0] * acc), (float)((double)rho.y * L.power[1] * acc),
+                          (float)((double)rho.z * L.power[2] * acc)),
+              fmt);
 }
 
 // orthonormal basis around a unit vector (Duff et al., JCGT 2017) and
@@ -308,20 +318,17 @@ __global__ void ir_paths_kernel(const uint32_t *c_valid, const uint32_t *rank, i
 
 __global__ void ir_emit_kernel(GenArgs g, const float4 *c_pos, const float4 *c_nrm, const double *c_thr,
                                const uint32_t *c_valid, const uint32_t *rank, int64_t n_slots,
-                               const GenInfoDev *info, float4 *pos, void *nrm, void *flux, int fmt,
-                               float flux_scale)
+                               const GenInfoDev *info, float4 *pos, void *nrm, void *flux, int fmt)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_slots || !c_valid[i] || rank[i] >= (uint32_t)g.m_far) return;
     const int64_t v = g.m_close + rank[i];
     const double P = (double)info->paths;
-    pos[v] = c_pos[i];
-    store_attr(nrm, v, c_nrm[i], fmt);
-    store_attr(flux, v,
-               make_float4((float)(g.light.power[0] * c_thr[3 * i] / P * flux_scale),
-                           (float)(g.light.power[1] * c_thr[3 * i + 1] / P * flux_scale),
-                           (float)(g.light.power[2] * c_thr[3 * i + 2] / P * flux_scale), 0.0f),
-               fmt);
+    const float4 cp = c_pos[i], cn = c_nrm[i];
+    store_vpl(pos, nrm, flux, v, f3(cp), __float_as_int(cp.w), f3(cn), __float_as_int(cn.w),
+              make_float3((float)(g.light.power[0] * c_thr[3 * i] / P), (float)(g.light.power[1] * c_thr[3 * i + 1] / P),
+                          (float)(g.light.power[2] * c_thr[3 * i + 2] / P)),
+              fmt);
 }
 
 // far VPL rows that no path filled (only when the path budget ran out)
@@ -329,10 +336,8 @@ __global__ void far_tail_kernel(GenArgs g, const GenInfoDev *info, float4 *pos, 
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.m_far || i < info->m_far_kept) return;
-    const int64_t v = g.m_close + i;
-    pos[v] = make_float4(0, 0, 0, __int_as_float(-1));
-    store_attr(nrm, v, make_float4(0, 0, 0, __int_as_float(-1)), fmt);
-    store_attr(flux, v, make_float4(0, 0, 0, 0), fmt);
+    const float3 z = make_float3(0.0f, 0.0f, 0.0f);
+    store_vpl(pos, nrm, flux, g.m_close + i, z, -1, z, -1, z, fmt);
 }
 
 cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, float4 *pos, void *nrm,
@@ -340,7 +345,6 @@ cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, 
 {
     const int T = s.n_tris;
     const int TB = kGenThreads;
-    const float flux_scale = 1.0f;
     VPL_TRY(cudaMemsetAsync(info, 0, sizeof(GenInfoDev), ex.stream));
     Tmp flag, fpos;
     VPL_TRY(flag.alloc(ex, sizeof(uint32_t) * T));
@@ -380,7 +384,7 @@ cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, 
         VPL_LAUNCHED(ex);
         patch_kernel<<<grid_for(g.m_close, TB), TB, 0, ex.stream>>>(s, g, vals.as<uint32_t>(),
                                                                     F.as<unsigned long long>(), n_close, info, pos,
-                                                                    nrm, flux, fmt, flux_scale, ex.status);
+                                                                    nrm, flux, fmt, ex.status);
         VPL_LAUNCHED(ex);
     } else {
         Tmp F0;
@@ -411,7 +415,7 @@ cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, 
         ir_emit_kernel<<<grid_for(n_slots, 256), 256, 0, ex.stream>>>(g, cp.as<float4>(), cn.as<float4>(),
                                                                       ct.as<double>(), cv.as<uint32_t>(),
                                                                       rk.as<uint32_t>(), n_slots, info, pos, nrm,
-                                                                      flux, fmt, flux_scale);
+                                                                      flux, fmt);
         VPL_LAUNCHED(ex);
         far_tail_kernel<<<grid_for(g.m_far, 256), 256, 0, ex.stream>>>(g, info, pos, nrm, flux, fmt);
         VPL_LAUNCHED(ex);
