@@ -1,0 +1,85 @@
+"""The large configuration: ~1M-triangle dense clutter, 1920 x 1080 pixels,
+32768 VPLs (26214 patch / 6554 instant radiosity).  One full-size render on
+the GPU; the oracle checks sampled pixels of the 256 x 144 crop, the close
+set and the patch triangle assignment (exact), and the precision variants on
+the crop."""
+import numpy as np
+import pytest
+
+from paper_2203_11484_gb300 import workloads as W
+import parity as PY
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def large(orc):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11484_gb300 import build, vpl
+    build.build_library()
+    ctx = vpl.Context(0)
+    wl = W.room1m_workload()
+    sid = ctx.upload(wl.scene)
+    yield vpl, ctx, wl, sid, orc.OracleScene(wl.scene)
+    ctx.close()
+
+
+def _crop_pixels(wl, n, seed):
+    x0, y0, w, h = wl.crop
+    W_ = wl.views[0].camera.width
+    rng = np.random.default_rng(seed)
+    xs = x0 + rng.integers(0, w, n)
+    ys = y0 + rng.integers(0, h, n)
+    return np.unique(ys * W_ + xs)
+
+
+def test_large_scene_builds(large):
+    V, ctx, wl, sid, _ = large
+    info = V.vpl_scene_query(ctx.h, sid)
+    assert info["n_tris"] == wl.scene.n_tris >= 1_000_000
+    assert 0 < info["depth"] <= 96
+
+
+def test_large_generation_exact_assignment(large):
+    V, ctx, wl, sid, osc = large
+    view = wl.views[0]
+    M = view.gen.m_close + view.gen.m_far
+    vs = V.VplSet.empty(M)
+    V.vpl_generate(ctx.h, sid, view.camera, view.gen, vs)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    info = V.vpl_generate_info(ctx.h)
+    r = osc.generate(view.camera, view.gen, vis_mode=0)
+    assert r["status"] == 0
+    assert info["n_close"] == r["n_close"] > 0
+    assert info["f_total"] == r["f_total"]
+    tri = vs.pos.cpu().numpy()[:, 3].copy().view(np.int32)
+    Mc = view.gen.m_close
+    assert np.array_equal(tri[:Mc], r["tri"][:Mc])
+    pos = vs.pos.cpu().numpy()[:Mc, :3].astype(np.float64)
+    assert np.abs(pos - r["pos"][:Mc]).max() <= PY.POS_TOL * wl.scene.diag()
+
+
+def test_large_render_full_size_crop_parity(large):
+    V, ctx, wl, sid, osc = large
+    import oracle as O
+    view = wl.views[0]
+    cam = view.camera
+    out = torch.zeros((cam.width * cam.height, 4), dtype=torch.float32, device="cuda")
+    V.vpl_render(ctx.h, sid, cam, view.gen, view.gather, out)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    img = out.cpu().numpy()
+    assert np.isfinite(img).all()
+    pix = _crop_pixels(wl, 96, 3)
+    r = O.render(osc, view, pix)
+    gb = V.GBuffer.empty(cam.width, cam.height)
+    V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
+    V.vpl_sync(ctx.h)
+    gtri = gb.pos.cpu().numpy()[pix, 3].copy().view(np.int32)
+    same = gtri == r["gbuffer"]["tri"]
+    assert same.mean() >= 0.98
+    bad = PY.pixel_fail(img[pix], r["image"]) & same
+    assert bad.mean() <= 0.03, int(bad.sum())
+    assert r["image"].max() > 0
