@@ -141,6 +141,63 @@ def cpu_baseline(workload, seconds: float = 12.0) -> dict:
                       f"incl. G-buffer of those pixels and full VPL generation, {t_used:.1f} s"}
 
 
+def batch_section(ctx, n_views: int, precision: int, reps: int = 2) -> dict:
+    """Many close-up views of the resident 200k-triangle room with uneven
+    resolutions and VPL budgets: one vpl_render per view (one launch sequence
+    each) against the batched path (G-buffers and VPLs per view, one
+    persistent gather for all views, autotuned tile shape, captured in a CUDA
+    graph).  Same images either way."""
+    import torch
+    from paper_2203_11484_gb300 import batch as BT
+    from paper_2203_11484_gb300 import vpl as V
+    from paper_2203_11484_gb300 import workloads as W
+    wl = W.batch_views(n_views=n_views, precision=precision)
+    sc = wl.scene
+    sid = V.vpl_scene_upload(ctx.h, torch.as_tensor(sc.verts).cuda(), torch.as_tensor(sc.tris).cuda(),
+                             torch.as_tensor(sc.albedo).cuda(), sc.light)
+    V.vpl_sync(ctx.h)
+    stream = torch.cuda.current_stream()
+    outs = [torch.zeros((v.camera.width * v.camera.height, 4), dtype=torch.float32, device="cuda")
+            for v in wl.views]
+
+    def single():
+        for v, o in zip(wl.views, outs):
+            V.vpl_render(ctx.h, sid, v.camera, v.gen, v.gather, o, stream)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_single = timed(single)
+    # tune on the first 16 views (same distribution), then the whole batch
+    tuner = BT.BatchRenderer(ctx.h, sid, wl.views[:16], precision)
+    cfg = tuner.autotune(candidates=[(8, 0), (4, 0), (16, 0), (8, 4)])
+    tuner.close()
+    br = BT.BatchRenderer(ctx.h, sid, wl.views, precision)
+    br.config = cfg
+    br.capture(include_generation=True)
+    ms_batch = timed(br.replay)
+    same = all(torch.equal(a, b) for a, b in zip(outs, br.outs))
+    pairs = br.pairs()
+    br.close()
+    status = V.vpl_sync(ctx.h, check=False)  # a view without close-range faces reports EMPTY_CLOSE
+    V.vpl_scene_release(ctx.h, sid)
+    return {"workload": wl.name, "views": n_views, "pairs": pairs,
+            "single_view_ms": ms_single, "batched_graph_ms": ms_batch,
+            "views_per_s_single": n_views / (ms_single / 1e3), "views_per_s_batched": n_views / (ms_batch / 1e3),
+            "pairs_per_s_batched": pairs / (ms_batch / 1e3), "speedup": ms_single / ms_batch,
+            "tuned": {"tile_w": cfg[0], "blocks_per_sm": cfg[1]}, "images_identical": bool(same),
+            "device_status": V.STATUS_NAMES.get(status, status),
+            "graph": "G-buffers + VPL generation per view + one batched gather, captured once"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores, steps of a
     bounded sample of the same workload."""
@@ -339,6 +396,10 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": hout.numel() * 4,
                "ms_per_step": statistics.mean(e_ms)}
 
+    batch = None
+    if args.batch_views > 0 and args.workload == "room200k":
+        batch = batch_section(ctx, args.batch_views, prec)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -359,7 +420,7 @@ def run_ours(args):
                 "views_per_s": ws * args.steps / (total_ms / 1e3),
                 "gather_ms_per_step": gather_in_step_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk, "wall_s": wall}
+                "gpu_launches": int(launches), "clocks": clk, "wall_s": wall, "batch": batch}
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
@@ -377,6 +438,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch-views", type=int, default=64,
+                    help="views of the batched comparison (0: skip)")
     ap.add_argument("--workload", default="room200k", choices=["room200k", "clutter1m"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16_kahan", "fp16_plain"])
     ap.add_argument("--width", type=int, default=0, help="0: the workload's size")

@@ -125,10 +125,16 @@ typedef struct {
  *  d2_min     lower clamp of the squared distance in the geometry term
  *  ray_eps    offset of both shadow-ray end points along their normals
  *  precision  VPL_PREC_*: FP32, or FP16 attributes with Kahan / plain FP32 sums
- *  visibility VPL_VIS_*: BVH shadow rays, all-triangle test, or none (V = 1) */
+ *  visibility VPL_VIS_*: BVH shadow rays, all-triangle test, or none (V = 1)
+ *  tile_w     pixel tile of one warp: tile_w x (32 / tile_w), tile_w in
+ *             {4, 8, 16, 32}; 0 = 8 (8 x 4)
+ *  blocks_per_sm  cap on resident blocks per SM of the persistent grid
+ *             (0 = as many as fit).  tile_w and blocks_per_sm change speed
+ *             only, never the result. */
 typedef struct {
     float d2_min, ray_eps;
     int32_t precision, visibility;
+    int32_t tile_w, blocks_per_sm;
 } vpl_gather_params;
 
 /* caller-owned device buffers (see the layouts above) */
@@ -219,6 +225,24 @@ VPL_API int vpl_gather(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf
 VPL_API int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf,
                                const vpl_vpl_set *vpls, const vpl_gather_params *params,
                                float *out_rgba, vpl_stream stream);
+
+/* Batched step (4): many views, each with its own G-buffer, VPL set and
+ * image (resolutions and VPL counts may differ), gathered by ONE persistent
+ * launch whose warps take 32-pixel tiles of all views from one queue, views
+ * with the most VPLs first.  vpl_batch_create copies a device table of the
+ * views (synchronously; the buffers must stay allocated while the batch is
+ * used) and fixes the tile width (tile_w as in vpl_gather_params, 0 = 8);
+ * vpl_gather_batch then enqueues only a memset and one kernel, so it can be
+ * captured in a CUDA graph.  Each pixel's sum runs in VPL order within one
+ * thread: images equal those of vpl_gather per view.  Calls with the same
+ * batch must not overlap on the GPU (they share its tile counter). */
+typedef uint64_t vpl_batch_id;
+VPL_API int vpl_batch_create(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs,
+                             const vpl_vpl_set *vpls, float *const *out_rgba, int32_t tile_w,
+                             vpl_batch_id *out);
+VPL_API int vpl_batch_destroy(vpl_ctx *ctx, vpl_batch_id batch);
+VPL_API int vpl_gather_batch(vpl_ctx *ctx, vpl_scene_id scene, vpl_batch_id batch,
+                             const vpl_gather_params *params, vpl_stream stream);
 
 /* Steps (1)-(4) with library-held temporaries: G-buffer, VPLs, gather. */
 VPL_API int vpl_render(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam,

@@ -2,11 +2,13 @@
 // registry, argument checks, the camera frame, and the order of launches of
 // each pipeline step.  Host code here is compiled with -ffp-contract=off: the
 // camera frame feeds the exact FP64 close-range decisions.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
+#include <vector>
 
 #include "vpl_internal.h"
 
@@ -41,6 +43,13 @@ struct vpl_ctx {
     cudaEvent_t ev[6] = {};
     bool ev_valid[6] = {};
     cudaMemPool_t pool = nullptr;
+    struct Batch {
+        ViewDesc *views = nullptr; // device table, sorted by first tile
+        int *counter = nullptr;    // the launch's tile counter
+        int n_views = 0, n_tiles = 0, tile_shift = 3;
+    };
+    std::map<uint64_t, Batch> batches;
+    uint64_t next_batch = 1;
 };
 
 namespace {
@@ -219,6 +228,9 @@ int check_gather(vpl_ctx *ctx, const vpl_gather_params *p, int gfmt, int vfmt)
     if (p->precision < 0 || p->precision > 2) return fail(ctx, VPL_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
     if (!(p->d2_min >= 0.0f) || !std::isfinite(p->d2_min)) return fail(ctx, VPL_ERR_INVALID_ARG, "d2_min must be >= 0");
     if (!(p->ray_eps >= 0.0f) || !std::isfinite(p->ray_eps)) return fail(ctx, VPL_ERR_INVALID_ARG, "ray_eps must be >= 0");
+    if (p->tile_w != 0 && p->tile_w != 4 && p->tile_w != 8 && p->tile_w != 16 && p->tile_w != 32)
+        return fail(ctx, VPL_ERR_INVALID_ARG, "tile_w must be 0, 4, 8, 16 or 32");
+    if (p->blocks_per_sm < 0) return fail(ctx, VPL_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
     int want = p->precision == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     if (gfmt != want || vfmt != want)
         return fail(ctx, VPL_ERR_INVALID_ARG, "buffer formats must be FP32 for precision 0 and FP16 otherwise");
@@ -288,6 +300,8 @@ GatherArgs gather_args(const vpl_gbuffer *g, const vpl_vpl_set *v, const vpl_gat
     a.ray_eps = p->ray_eps;
     a.precision = p->precision;
     a.visibility = p->visibility;
+    a.tile_w = p->tile_w;
+    a.blocks_per_sm = p->blocks_per_sm;
     a.g_pos = (const float4 *)g->pos;
     a.g_nrm = g->nrm;
     a.g_alb = g->albedo;
@@ -340,6 +354,11 @@ void vpl_destroy(vpl_ctx *ctx)
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
+    for (auto &kv : ctx->batches) {
+        cudaFree(kv.second.views);
+        cudaFree(kv.second.counter);
+    }
+    ctx->batches.clear();
     for (auto &kv : ctx->scenes) {
         free_scene(kv.second->b);
         delete kv.second;
@@ -506,7 +525,9 @@ int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf
     if ((rc = check_vpls(ctx, vpls))) return rc;
     if ((rc = check_gather(ctx, params, gbuf->format, vpls->format))) return rc;
     if ((int64_t)gbuf->width * gbuf->height > 0 && !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "out_rgba is NULL");
-    const int64_t tiles = (((int64_t)gbuf->width + 7) / 8) * (((int64_t)gbuf->height + 3) / 4);
+    const int tsh = tile_shift_of(params->tile_w);
+    const int64_t tw = (int64_t)1 << tsh, th = 32 >> tsh;
+    const int64_t tiles = (((int64_t)gbuf->width + tw - 1) / tw) * (((int64_t)gbuf->height + th - 1) / th);
     if (tiles > gather_noalloc_max_tiles())
         return fail(ctx, VPL_ERR_INVALID_ARG,
                     "vpl_gather_noalloc: image has more than 2^30 tiles of 8x4 pixels, the most its static "
@@ -514,6 +535,108 @@ int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf
     DeviceGuard g(ctx->device);
     Exec ex = exec_of(ctx, stream);
     CK(ctx, gather_noalloc(ex, view_of(s), gather_args(gbuf, vpls, params, out_rgba)), "vpl_gather_noalloc");
+    return VPL_OK;
+}
+
+int vpl_batch_create(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, const vpl_vpl_set *vpls,
+                     float *const *out_rgba, int32_t tile_w, vpl_batch_id *out)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    if (!out) return fail(ctx, VPL_ERR_INVALID_ARG, "out is NULL");
+    *out = 0;
+    if (n_views < 1 || !gbufs || !vpls || !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "bad batch arrays");
+    if (tile_w != 0 && tile_w != 4 && tile_w != 8 && tile_w != 16 && tile_w != 32)
+        return fail(ctx, VPL_ERR_INVALID_ARG, "tile_w must be 0, 4, 8, 16 or 32");
+    int fmt = gbufs[0].format;
+    for (int i = 0; i < n_views; i++) {
+        int rc = check_gbuffer(ctx, &gbufs[i], nullptr);
+        if (rc) return rc;
+        if ((rc = check_vpls(ctx, &vpls[i]))) return rc;
+        if (gbufs[i].format != fmt || vpls[i].format != fmt)
+            return fail(ctx, VPL_ERR_INVALID_ARG, "all views of a batch need one format");
+        if ((int64_t)gbufs[i].width * gbufs[i].height > 0 && !out_rgba[i])
+            return fail(ctx, VPL_ERR_INVALID_ARG, "out_rgba[i] is NULL");
+    }
+    const int tsh = tile_shift_of(tile_w);
+    const int64_t tw = (int64_t)1 << tsh, th = 32 >> tsh;
+    // views with the most VPLs per tile first: their tiles are the longest
+    std::vector<int> order(n_views);
+    for (int i = 0; i < n_views; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return vpls[a].count > vpls[b].count; });
+    std::vector<ViewDesc> h(n_views);
+    int64_t tiles = 0;
+    for (int k = 0; k < n_views; k++) {
+        const int i = order[k];
+        ViewDesc &d = h[k];
+        memset(&d, 0, sizeof d);
+        d.width = gbufs[i].width;
+        d.height = gbufs[i].height;
+        d.count = vpls[i].count;
+        d.tiles_x = (int32_t)((gbufs[i].width + tw - 1) / tw);
+        d.tile_begin = (int32_t)tiles;
+        d.g_pos = (const float4 *)gbufs[i].pos;
+        d.g_nrm = gbufs[i].nrm;
+        d.g_alb = gbufs[i].albedo;
+        d.v_pos = (const float4 *)vpls[i].pos;
+        d.v_nrm = vpls[i].nrm;
+        d.v_flux = vpls[i].flux;
+        d.out = (float4 *)out_rgba[i];
+        tiles += (int64_t)d.tiles_x * ((gbufs[i].height + th - 1) / th);
+        if (tiles > ((int64_t)1 << 30)) return fail(ctx, VPL_ERR_INVALID_ARG, "batch has more than 2^30 tiles");
+    }
+    DeviceGuard g(ctx->device);
+    vpl_ctx::Batch b;
+    b.n_views = n_views;
+    b.n_tiles = (int)tiles;
+    b.tile_shift = tsh;
+    CK(ctx, cudaMalloc(&b.views, sizeof(ViewDesc) * n_views), "vpl_batch_create");
+    if (cudaMalloc(&b.counter, sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(b.views, h.data(), sizeof(ViewDesc) * n_views, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(b.views);
+        if (b.counter) cudaFree(b.counter);
+        return cuda_fail(ctx, cudaErrorMemoryAllocation, "vpl_batch_create");
+    }
+    const uint64_t id = ctx->next_batch++;
+    ctx->batches[id] = b;
+    *out = id;
+    return VPL_OK;
+}
+
+int vpl_batch_destroy(vpl_ctx *ctx, vpl_batch_id batch)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    auto it = ctx->batches.find(batch);
+    if (it == ctx->batches.end()) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown batch id");
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(it->second.views);
+    cudaFree(it->second.counter);
+    ctx->batches.erase(it);
+    return VPL_OK;
+}
+
+int vpl_gather_batch(vpl_ctx *ctx, vpl_scene_id scene, vpl_batch_id batch, const vpl_gather_params *params,
+                     vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    auto it = ctx->batches.find(batch);
+    if (it == ctx->batches.end()) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown batch id");
+    const int fmt = params && params->precision != VPL_PREC_FP32 ? VPL_FORMAT_FP16 : VPL_FORMAT_FP32;
+    int rc = check_gather(ctx, params, fmt, fmt);
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    GatherArgs a;
+    memset(&a, 0, sizeof a);
+    a.d2_min = params->d2_min;
+    a.ray_eps = params->ray_eps;
+    a.precision = params->precision;
+    a.visibility = params->visibility;
+    a.blocks_per_sm = params->blocks_per_sm;
+    const vpl_ctx::Batch &b = it->second;
+    CK(ctx, gather_batch(exec_of(ctx, stream), view_of(s), a, b.views, b.n_views, b.n_tiles, b.tile_shift, b.counter),
+       "vpl_gather_batch");
     return VPL_OK;
 }
 

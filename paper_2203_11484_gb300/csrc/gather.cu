@@ -92,21 +92,22 @@ cudaError_t gbuffer_build(const Exec &ex, const SceneView &s, const CamArgs &c, 
 // ==========================================================================
 struct GatherExtra {
     int *tile_counter;
-    int n_tiles, tiles_x;
-    unsigned long long *counters; // COUNT
-    const int32_t *dbg_pixels;    // DEBUG: pixel list, else null
+    int n_tiles, tiles_x, tile_shift; // tile_w = 1 << tile_shift pixels, tile_h = 32 / tile_w
+    const ViewDesc *views;            // BATCH: view table sorted by tile_begin
+    int n_views;
+    unsigned long long *counters;     // COUNT
+    const int32_t *dbg_pixels;        // DEBUG: pixel list, else null
     int64_t n_dbg;
     int8_t *dbg_vis;
 };
 
-template <int VIS, int PREC, bool COUNT, bool DEBUG>
+template <int VIS, int PREC, bool COUNT, bool DEBUG, bool BATCH>
 __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gather_kernel(SceneView s, GatherArgs a, GatherExtra e, int *status)
 {
     __shared__ float4 stage[kGatherWarps][3][32];
     __shared__ int stack[kGatherWarps][kStackMax]; // per-warp traversal stacks
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gfmt = PREC == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
-    const int M = a.count;
     const float eps = a.ray_eps, d2min = a.d2_min;
     WarpCounters wc = {0u, 0u, 0u};
     unsigned long long n_pairs = 0, n_rays = 0, n_blocked = 0;
@@ -115,6 +116,31 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
         if (lane == 0) tile = atomicAdd(e.tile_counter, 1);
         tile = __shfl_sync(kFull, tile, 0);
         if (tile >= e.n_tiles) break;
+        // the view this tile belongs to
+        int width = a.width, height = a.height, M = a.count, tiles_x = e.tiles_x, lt = tile;
+        const float4 *g_pos = a.g_pos, *v_pos = a.v_pos;
+        const void *g_nrm = a.g_nrm, *g_alb = a.g_alb, *v_nrm = a.v_nrm, *v_flux = a.v_flux;
+        float4 *out = a.out;
+        if (BATCH) {
+            int lo = 0, hi = e.n_views;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (e.views[mid].tile_begin <= tile) lo = mid; else hi = mid;
+            }
+            const ViewDesc *vd = e.views + lo;
+            width = vd->width;
+            height = vd->height;
+            M = vd->count;
+            tiles_x = vd->tiles_x;
+            lt = tile - vd->tile_begin;
+            g_pos = vd->g_pos;
+            g_nrm = vd->g_nrm;
+            g_alb = vd->g_alb;
+            v_pos = vd->v_pos;
+            v_nrm = vd->v_nrm;
+            v_flux = vd->v_flux;
+            out = vd->out;
+        }
         int64_t p;
         bool inb; // pixel exists (in the image / in the debug list)
         if (DEBUG) {
@@ -122,14 +148,15 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
             inb = q < e.n_dbg;
             p = inb ? e.dbg_pixels[q] : 0;
         } else {
-            int px = (tile % e.tiles_x) * kTileW + (lane & (kTileW - 1));
-            int py = (tile / e.tiles_x) * kTileH + (lane / kTileW);
-            inb = px < a.width && py < a.height;
-            p = inb ? (int64_t)py * a.width + px : 0;
+            const int tw = 1 << e.tile_shift, th = 32 >> e.tile_shift;
+            const int px = (lt % tiles_x) * tw + (lane & (tw - 1));
+            const int py = (lt / tiles_x) * th + (lane >> e.tile_shift);
+            inb = px < width && py < height;
+            p = inb ? (int64_t)py * width + px : 0;
         }
-        float4 gp = inb ? __ldg(a.g_pos + p) : make_float4(0, 0, 0, __int_as_float(-1));
+        float4 gp = inb ? __ldg(g_pos + p) : make_float4(0, 0, 0, __int_as_float(-1));
         const bool valid = inb && __float_as_int(gp.w) >= 0;
-        float4 gn = valid ? load_attr(a.g_nrm, p, gfmt) : make_float4(0, 0, 0, 0);
+        float4 gn = valid ? load_attr(g_nrm, p, gfmt) : make_float4(0, 0, 0, 0);
         const float3 y = f3(gp), ny = f3(gn);
         const float3 o = y + ny * eps;
         int occ_cache = -1;                    // last blocking triangle of this pixel
@@ -141,15 +168,15 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
             if (__shfl_sync(kFull, st, 0) != 0) break;
             const int i = base + lane;
             if (i < M) {
-                const float4 vp = __ldg(a.v_pos + i);
-                float4 vf = load_attr(a.v_flux, i, gfmt);
+                const float4 vp = __ldg(v_pos + i);
+                float4 vf = load_attr(v_flux, i, gfmt);
                 if (gfmt == VPL_FORMAT_FP16) { // FP16 colour x FP32 magnitude (pos.w)
                     vf.x *= vp.w;
                     vf.y *= vp.w;
                     vf.z *= vp.w;
                 }
                 stage[wid][0][lane] = vp;
-                stage[wid][1][lane] = load_attr(a.v_nrm, i, gfmt);
+                stage[wid][1][lane] = load_attr(v_nrm, i, gfmt);
                 stage[wid][2][lane] = vf;
             }
             __syncwarp();
@@ -193,10 +220,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
             }
             __syncwarp();
         }
-        if (!DEBUG && inb && a.out) {
-            float4 rho = valid ? load_attr(a.g_alb, p, gfmt) : make_float4(0, 0, 0, 0);
+        if (!DEBUG && inb && out) {
+            float4 rho = valid ? load_attr(g_alb, p, gfmt) : make_float4(0, 0, 0, 0);
             const float k = 1.0f / (kPi * kPi);
-            a.out[p] = make_float4(rho.x * ax * k, rho.y * ay * k, rho.z * az * k, 0.0f);
+            out[p] = make_float4(rho.x * ax * k, rho.y * ay * k, rho.z * az * k, 0.0f);
         }
     }
     if (COUNT) {
@@ -210,16 +237,18 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
     }
 }
 
-template <int VIS, int PREC, bool COUNT, bool DEBUG>
+template <int VIS, int PREC, bool COUNT, bool DEBUG, bool BATCH>
 static cudaError_t launch_gather(const Exec &ex, const SceneView &s, const GatherArgs &a, GatherExtra e)
 {
-    auto kern = gather_kernel<VIS, PREC, COUNT, DEBUG>;
+    auto kern = gather_kernel<VIS, PREC, COUNT, DEBUG, BATCH>;
     int dev = 0, sms = 0, per_sm = 0;
     VPL_TRY(cudaGetDevice(&dev));
     VPL_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     VPL_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherWarps * 32, 0));
+    if (per_sm < 1) per_sm = 1;
+    if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
     int64_t want = (e.n_tiles + kGatherWarps - 1) / kGatherWarps;
-    int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    int64_t cap = (int64_t)sms * per_sm;
     unsigned grid = (unsigned)(want < cap ? want : cap);
     if (grid == 0) grid = 1;
     kern<<<grid, kGatherWarps * 32, 0, ex.stream>>>(s, a, e, ex.status);
@@ -227,11 +256,11 @@ static cudaError_t launch_gather(const Exec &ex, const SceneView &s, const Gathe
     return cudaSuccess;
 }
 
-template <bool COUNT, bool DEBUG>
+template <bool COUNT, bool DEBUG, bool BATCH>
 static cudaError_t dispatch(const Exec &ex, const SceneView &s, const GatherArgs &a, GatherExtra e)
 {
 #define VPL_CASE(V, P)                                                                  \
-    if (a.visibility == V && a.precision == P) return launch_gather<V, P, COUNT, DEBUG>(ex, s, a, e);
+    if (a.visibility == V && a.precision == P) return launch_gather<V, P, COUNT, DEBUG, BATCH>(ex, s, a, e);
     VPL_CASE(VPL_VIS_BVH, VPL_PREC_FP32)
     VPL_CASE(VPL_VIS_BRUTE, VPL_PREC_FP32)
     VPL_CASE(VPL_VIS_NONE, VPL_PREC_FP32)
@@ -245,6 +274,33 @@ static cudaError_t dispatch(const Exec &ex, const SceneView &s, const GatherArgs
     return cudaErrorInvalidValue;
 }
 
+int tile_shift_of(int tile_w)
+{
+    switch (tile_w) {
+    case 4: return 2;
+    case 16: return 4;
+    case 32: return 5;
+    default: return 3; // 8 x 4
+    }
+}
+
+static GatherExtra single_view_extra(const GatherArgs &a, int *counter)
+{
+    GatherExtra e;
+    e.tile_counter = counter;
+    e.tile_shift = tile_shift_of(a.tile_w);
+    const int tw = 1 << e.tile_shift, th = 32 >> e.tile_shift;
+    e.tiles_x = (a.width + tw - 1) / tw;
+    e.n_tiles = e.tiles_x * ((a.height + th - 1) / th);
+    e.views = nullptr;
+    e.n_views = 0;
+    e.counters = nullptr;
+    e.dbg_pixels = nullptr;
+    e.n_dbg = 0;
+    e.dbg_vis = nullptr;
+    return e;
+}
+
 static cudaError_t run_gather(const Exec &ex, const SceneView &s, const GatherArgs &a, bool count,
                               unsigned long long *counters, const int32_t *pixels, int64_t n_pixels, int8_t *vis)
 {
@@ -254,17 +310,29 @@ static cudaError_t run_gather(const Exec &ex, const SceneView &s, const GatherAr
     Tmp ctr;
     VPL_TRY(ctr.alloc(ex, sizeof(int)));
     VPL_TRY(cudaMemsetAsync(ctr.p, 0, sizeof(int), ex.stream));
-    GatherExtra e;
-    e.tile_counter = ctr.as<int>();
-    e.tiles_x = (a.width + kTileW - 1) / kTileW;
-    e.n_tiles = pixels ? (int)((n_pixels + 31) / 32) : e.tiles_x * ((a.height + kTileH - 1) / kTileH);
+    GatherExtra e = single_view_extra(a, ctr.as<int>());
+    if (pixels) e.n_tiles = (int)((n_pixels + 31) / 32);
     e.counters = counters;
     e.dbg_pixels = pixels;
     e.n_dbg = n_pixels;
     e.dbg_vis = vis;
-    if (pixels) return dispatch<false, true>(ex, s, a, e);
-    if (count) return dispatch<true, false>(ex, s, a, e);
-    return dispatch<false, false>(ex, s, a, e);
+    if (pixels) return dispatch<false, true, false>(ex, s, a, e);
+    if (count) return dispatch<true, false, false>(ex, s, a, e);
+    return dispatch<false, false, false>(ex, s, a, e);
+}
+
+// many views in one persistent launch: tiles of all views in one queue
+cudaError_t gather_batch(const Exec &ex, const SceneView &s, const GatherArgs &a, const ViewDesc *views, int n_views,
+                         int n_tiles, int tile_shift, int *counter)
+{
+    if (n_tiles == 0) return cudaSuccess;
+    VPL_TRY(cudaMemsetAsync(counter, 0, sizeof(int), ex.stream));
+    GatherExtra e = single_view_extra(a, counter);
+    e.views = views;
+    e.n_views = n_views;
+    e.n_tiles = n_tiles;
+    e.tile_shift = tile_shift;
+    return dispatch<false, false, true>(ex, s, a, e);
 }
 
 cudaError_t gather(const Exec &ex, const SceneView &s, const GatherArgs &a)
@@ -318,15 +386,7 @@ cudaError_t gather_noalloc(const Exec &ex, const SceneView &s, const GatherArgs 
     }
     // the array keeps the previous call's counter: start this one at zero
     VPL_TRY(cudaMemsetAsync(scratch, 0, sizeof(int), ex.stream));
-    GatherExtra e;
-    e.tile_counter = scratch;
-    e.tiles_x = (a.width + kTileW - 1) / kTileW;
-    e.n_tiles = e.tiles_x * ((a.height + kTileH - 1) / kTileH);
-    e.counters = nullptr;
-    e.dbg_pixels = nullptr;
-    e.n_dbg = 0;
-    e.dbg_vis = nullptr;
-    return dispatch<false, false>(ex, s, a, e);
+    return dispatch<false, false, false>(ex, s, a, single_view_extra(a, scratch));
 }
 
 int64_t gather_noalloc_max_tiles() { return (int64_t)1 << 30; }

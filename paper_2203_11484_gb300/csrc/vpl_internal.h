@@ -111,12 +111,31 @@ struct GatherArgs {
     int32_t width, height, count;
     float d2_min, ray_eps;
     int32_t precision, visibility;
+    int32_t tile_w;        // pixel tile width of a warp (4, 8, 16, 32; 0 = 8)
+    int32_t blocks_per_sm; // resident blocks per SM of the persistent grid (0 = occupancy limit)
     const float4 *g_pos;
     const void *g_nrm, *g_alb;
     const float4 *v_pos;
     const void *v_nrm, *v_flux;
     float4 *out;
 };
+
+// one view of a batched gather (a device table built by vpl_batch_create,
+// views in order of their first tile)
+struct ViewDesc {
+    int32_t width, height, count, tiles_x;
+    int32_t tile_begin, pad0, pad1, pad2;
+    const float4 *g_pos;
+    const void *g_nrm, *g_alb;
+    const float4 *v_pos;
+    const void *v_nrm, *v_flux;
+    float4 *out;
+    const void *pad3;
+};
+
+int tile_shift_of(int tile_w);
+cudaError_t gather_batch(const Exec &ex, const SceneView &s, const GatherArgs &a, const ViewDesc *views, int n_views,
+                         int n_tiles, int tile_shift, int *counter);
 
 cudaError_t gbuffer_build(const Exec &ex, const SceneView &s, const CamArgs &c, bool brute,
                           float4 *pos, void *nrm, void *alb, int format);

@@ -50,7 +50,7 @@ class vpl_gen_params(C.Structure):
 
 class vpl_gather_params(C.Structure):
     _fields_ = [("d2_min", C.c_float), ("ray_eps", C.c_float), ("precision", C.c_int32),
-                ("visibility", C.c_int32)]
+                ("visibility", C.c_int32), ("tile_w", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 
 class vpl_vpl_set(C.Structure):
@@ -96,6 +96,10 @@ _SIGS = {
                              C.POINTER(vpl_gather_params), _P, _P]),
     "vpl_gather_noalloc": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_gbuffer), C.POINTER(vpl_vpl_set),
                                      C.POINTER(vpl_gather_params), _P, _P]),
+    "vpl_batch_create": (C.c_int, [_P, C.c_int32, C.POINTER(vpl_gbuffer), C.POINTER(vpl_vpl_set),
+                                   C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_uint64)]),
+    "vpl_batch_destroy": (C.c_int, [_P, C.c_uint64]),
+    "vpl_gather_batch": (C.c_int, [_P, C.c_uint64, C.c_uint64, C.POINTER(vpl_gather_params), _P]),
     "vpl_render": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_camera), C.POINTER(vpl_gen_params),
                              C.POINTER(vpl_gather_params), _P, _P]),
     "vpl_sync": (C.c_int, [_P, _P]),
@@ -195,6 +199,7 @@ def make_gather(p: W.GatherParams) -> vpl_gather_params:
     s = vpl_gather_params()
     s.d2_min, s.ray_eps = float(p.d2_min), float(p.ray_eps)
     s.precision, s.visibility = int(p.precision), int(p.visibility)
+    s.tile_w, s.blocks_per_sm = int(getattr(p, "tile_w", 0)), int(getattr(p, "blocks_per_sm", 0))
     return s
 
 
@@ -320,6 +325,25 @@ def vpl_gather_noalloc(ctx, scene: int, gbuf: GBuffer, vpls: VplSet, params: W.G
     gb, vs, p = gbuf.struct(), vpls.struct(), make_gather(params)
     _check(ctx, load().vpl_gather_noalloc(ctx, scene, C.byref(gb), C.byref(vs), C.byref(p), _ptr(out),
                                           _stream(stream)), "vpl_gather_noalloc")
+
+
+def vpl_batch_create(ctx, gbufs, vsets, outs, tile_w: int = 0) -> int:
+    n = len(gbufs)
+    gb = (vpl_gbuffer * n)(*[g.struct() for g in gbufs])
+    vs = (vpl_vpl_set * n)(*[v.struct() for v in vsets])
+    op = (C.c_void_p * n)(*[_ptr(o) for o in outs])
+    bid = C.c_uint64()
+    _check(ctx, load().vpl_batch_create(ctx, n, gb, vs, op, int(tile_w), C.byref(bid)), "vpl_batch_create")
+    return int(bid.value)
+
+
+def vpl_batch_destroy(ctx, batch: int) -> None:
+    _check(ctx, load().vpl_batch_destroy(ctx, batch), "vpl_batch_destroy")
+
+
+def vpl_gather_batch(ctx, scene: int, batch: int, params: W.GatherParams, stream=None) -> None:
+    p = make_gather(params)
+    _check(ctx, load().vpl_gather_batch(ctx, scene, batch, C.byref(p), _stream(stream)), "vpl_gather_batch")
 
 
 def vpl_render(ctx, scene: int, camera: W.Camera, gen: W.GenParams, params: W.GatherParams, out,

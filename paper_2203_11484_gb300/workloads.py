@@ -78,6 +78,8 @@ class GatherParams:
     ray_eps: float
     precision: int = PREC_FP32
     visibility: int = VIS_BVH
+    tile_w: int = 0           # warp pixel tile width (0 = 8): speed only
+    blocks_per_sm: int = 0    # persistent grid cap (0 = occupancy limit): speed only
 
 
 @dataclass
