@@ -198,6 +198,56 @@ def batch_section(ctx, n_views: int, precision: int, reps: int = 2) -> dict:
             "graph": "G-buffers + VPL generation per view + one batched gather, captured once"}
 
 
+def serve_section(ctx, n_requests: int, factors, precision: int) -> dict:
+    """Poisson arrivals of render requests over two resident scenes (the 200k
+    room and the ~1M-triangle clutter); resolution 256^2 .. 1920x1080, VPL
+    budgets log-uniform 1k .. 16k.  The rate is a multiple of the measured
+    one-at-a-time capacity.  Continuous batching (4 lanes, groups of up to 8,
+    one batched gather per group) against a plain FIFO queue (one request per
+    launch sequence, one at a time), on the same arrivals."""
+    import numpy as np
+    import torch
+    from paper_2203_11484_gb300 import serve as S
+    from paper_2203_11484_gb300 import vpl as V
+    from paper_2203_11484_gb300 import workloads as W
+    room, rlo, rhi = W.room200k_scene()
+    clut, clo, chi = W.room1m_scene()
+    scenes = {"room200k": (room, rlo, rhi, W.ROOM_D_CLOSE), "clutter1m": (clut, clo, chi, W.ROOM_D_CLOSE * 0.5)}
+    sids = {k: ctx.upload(v[0]) for k, v in scenes.items()}
+    n_tris = {k: v[0].n_tris for k, v in scenes.items()}
+
+    def requests(rate, seed=11):
+        return S.random_requests(np.random.default_rng(seed), scenes, n_requests, rate, precision=precision)
+
+    # capacity: the same kind of requests rendered one at a time
+    probe = requests(1.0, seed=5)[: max(8, n_requests // 4)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in probe:
+        c = r.view.camera
+        o = torch.empty((c.width * c.height, 4), dtype=torch.float32, device="cuda")
+        V.vpl_render(ctx.h, sids[r.scene], c, r.view.gen, r.view.gather, o)
+    torch.cuda.synchronize()
+    capacity = len(probe) / (time.perf_counter() - t0)
+    out = {"capacity_views_per_s": capacity, "requests_per_rate": n_requests, "rates": []}
+    for f in factors:
+        row = {"rate_factor": f, "rate_per_s": f * capacity}
+        for name, lanes, group in (("plain_fifo", 1, 1), ("continuous_batching", 4, 8)):
+            srv = S.Server(S.GpuBackend(ctx.h, sids, lanes), n_tris, lanes=lanes, max_group=group,
+                           reserve_bytes=4 << 30)
+            st = srv.run(requests(f * capacity))
+            torch.cuda.synchronize()
+            st["groups"] = srv.groups_launched
+            st["max_concurrent_groups"] = srv.max_concurrent_groups
+            row[name] = st
+        out["rates"].append(row)
+    status = V.vpl_sync(ctx.h, check=False)
+    for s in sids.values():
+        V.vpl_scene_release(ctx.h, s)
+    out["device_status"] = V.STATUS_NAMES.get(status, status)
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores, steps of a
     bounded sample of the same workload."""
@@ -399,6 +449,9 @@ def run_ours(args):
     batch = None
     if args.batch_views > 0 and args.workload == "room200k":
         batch = batch_section(ctx, args.batch_views, prec)
+    serving = None
+    if args.serve_requests > 0 and args.workload == "room200k":
+        serving = serve_section(ctx, args.serve_requests, [float(x) for x in args.serve_rates.split(",")], prec)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -420,7 +473,8 @@ def run_ours(args):
                 "views_per_s": ws * args.steps / (total_ms / 1e3),
                 "gather_ms_per_step": gather_in_step_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk, "wall_s": wall, "batch": batch}
+                "gpu_launches": int(launches), "clocks": clk, "wall_s": wall, "batch": batch,
+                "serving": serving}
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
@@ -440,6 +494,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-views", type=int, default=64,
                     help="views of the batched comparison (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests per arrival rate in the serving comparison (0: skip)")
+    ap.add_argument("--serve-rates", default="1.0,2.0",
+                    help="arrival rates as multiples of the one-at-a-time capacity")
     ap.add_argument("--workload", default="room200k", choices=["room200k", "clutter1m"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16_kahan", "fp16_plain"])
     ap.add_argument("--width", type=int, default=0, help="0: the workload's size")

@@ -244,6 +244,15 @@ VPL_API int vpl_batch_destroy(vpl_ctx *ctx, vpl_batch_id batch);
 VPL_API int vpl_gather_batch(vpl_ctx *ctx, vpl_scene_id scene, vpl_batch_id batch,
                              const vpl_gather_params *params, vpl_stream stream);
 
+/* The batched gather without a persistent batch: the view table is built on
+ * the host and copied to pool memory on `stream` by this call, so it costs no
+ * device-wide synchronisation (the serving loop's path; not capturable).
+ * Arguments as vpl_batch_create plus the gather parameters. */
+VPL_API int vpl_gather_views(vpl_ctx *ctx, vpl_scene_id scene, int32_t n_views,
+                             const vpl_gbuffer *gbufs, const vpl_vpl_set *vpls,
+                             float *const *out_rgba, const vpl_gather_params *params,
+                             vpl_stream stream);
+
 /* Steps (1)-(4) with library-held temporaries: G-buffer, VPLs, gather. */
 VPL_API int vpl_render(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam,
                const vpl_gen_params *gen, const vpl_gather_params *params, float *out_rgba,

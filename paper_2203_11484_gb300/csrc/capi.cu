@@ -538,12 +538,14 @@ int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf
     return VPL_OK;
 }
 
-int vpl_batch_create(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, const vpl_vpl_set *vpls,
-                     float *const *out_rgba, int32_t tile_w, vpl_batch_id *out)
+} // extern "C"
+
+namespace {
+// host view table of a batch: views with the most VPLs first, tile ranges
+// in that order
+int build_view_table(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, const vpl_vpl_set *vpls,
+                     float *const *out_rgba, int32_t tile_w, std::vector<ViewDesc> &h, int64_t &tiles)
 {
-    if (!ctx) return VPL_ERR_INVALID_ARG;
-    if (!out) return fail(ctx, VPL_ERR_INVALID_ARG, "out is NULL");
-    *out = 0;
     if (n_views < 1 || !gbufs || !vpls || !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "bad batch arrays");
     if (tile_w != 0 && tile_w != 4 && tile_w != 8 && tile_w != 16 && tile_w != 32)
         return fail(ctx, VPL_ERR_INVALID_ARG, "tile_w must be 0, 4, 8, 16 or 32");
@@ -559,12 +561,11 @@ int vpl_batch_create(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, co
     }
     const int tsh = tile_shift_of(tile_w);
     const int64_t tw = (int64_t)1 << tsh, th = 32 >> tsh;
-    // views with the most VPLs per tile first: their tiles are the longest
     std::vector<int> order(n_views);
     for (int i = 0; i < n_views; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return vpls[a].count > vpls[b].count; });
-    std::vector<ViewDesc> h(n_views);
-    int64_t tiles = 0;
+    h.assign(n_views, ViewDesc());
+    tiles = 0;
     for (int k = 0; k < n_views; k++) {
         const int i = order[k];
         ViewDesc &d = h[k];
@@ -584,11 +585,61 @@ int vpl_batch_create(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, co
         tiles += (int64_t)d.tiles_x * ((gbufs[i].height + th - 1) / th);
         if (tiles > ((int64_t)1 << 30)) return fail(ctx, VPL_ERR_INVALID_ARG, "batch has more than 2^30 tiles");
     }
+    return VPL_OK;
+}
+} // namespace
+
+extern "C" {
+
+int vpl_gather_views(vpl_ctx *ctx, vpl_scene_id scene, int32_t n_views, const vpl_gbuffer *gbufs,
+                     const vpl_vpl_set *vpls, float *const *out_rgba, const vpl_gather_params *params,
+                     vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    const int fmt = params && params->precision != VPL_PREC_FP32 ? VPL_FORMAT_FP16 : VPL_FORMAT_FP32;
+    int rc = check_gather(ctx, params, fmt, fmt);
+    if (rc) return rc;
+    std::vector<ViewDesc> h;
+    int64_t tiles = 0;
+    if ((rc = build_view_table(ctx, n_views, gbufs, vpls, out_rgba, params->tile_w, h, tiles))) return rc;
+    if (gbufs[0].format != fmt) return fail(ctx, VPL_ERR_INVALID_ARG, "buffer format does not match the precision");
+    DeviceGuard g(ctx->device);
+    Exec ex = exec_of(ctx, stream);
+    Tmp table, counter;
+    CK(ctx, table.alloc(ex, sizeof(ViewDesc) * n_views), "vpl_gather_views");
+    CK(ctx, counter.alloc(ex, sizeof(int)), "vpl_gather_views");
+    CK(ctx, cudaMemcpyAsync(table.p, h.data(), sizeof(ViewDesc) * n_views, cudaMemcpyHostToDevice, ex.stream),
+       "vpl_gather_views");
+    GatherArgs a;
+    memset(&a, 0, sizeof a);
+    a.d2_min = params->d2_min;
+    a.ray_eps = params->ray_eps;
+    a.precision = params->precision;
+    a.visibility = params->visibility;
+    a.blocks_per_sm = params->blocks_per_sm;
+    CK(ctx, gather_batch(ex, view_of(s), a, table.as<ViewDesc>(), n_views, (int)tiles,
+                         tile_shift_of(params->tile_w), counter.as<int>()),
+       "vpl_gather_views");
+    return VPL_OK;
+}
+
+int vpl_batch_create(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, const vpl_vpl_set *vpls,
+                     float *const *out_rgba, int32_t tile_w, vpl_batch_id *out)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    if (!out) return fail(ctx, VPL_ERR_INVALID_ARG, "out is NULL");
+    *out = 0;
+    std::vector<ViewDesc> h;
+    int64_t tiles = 0;
+    int rc = build_view_table(ctx, n_views, gbufs, vpls, out_rgba, tile_w, h, tiles);
+    if (rc) return rc;
     DeviceGuard g(ctx->device);
     vpl_ctx::Batch b;
     b.n_views = n_views;
     b.n_tiles = (int)tiles;
-    b.tile_shift = tsh;
+    b.tile_shift = tile_shift_of(tile_w);
     CK(ctx, cudaMalloc(&b.views, sizeof(ViewDesc) * n_views), "vpl_batch_create");
     if (cudaMalloc(&b.counter, sizeof(int)) != cudaSuccess ||
         cudaMemcpy(b.views, h.data(), sizeof(ViewDesc) * n_views, cudaMemcpyHostToDevice) != cudaSuccess) {

@@ -99,6 +99,8 @@ _SIGS = {
     "vpl_batch_create": (C.c_int, [_P, C.c_int32, C.POINTER(vpl_gbuffer), C.POINTER(vpl_vpl_set),
                                    C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_uint64)]),
     "vpl_batch_destroy": (C.c_int, [_P, C.c_uint64]),
+    "vpl_gather_views": (C.c_int, [_P, C.c_uint64, C.c_int32, C.POINTER(vpl_gbuffer), C.POINTER(vpl_vpl_set),
+                                   C.POINTER(C.c_void_p), C.POINTER(vpl_gather_params), _P]),
     "vpl_gather_batch": (C.c_int, [_P, C.c_uint64, C.c_uint64, C.POINTER(vpl_gather_params), _P]),
     "vpl_render": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_camera), C.POINTER(vpl_gen_params),
                              C.POINTER(vpl_gather_params), _P, _P]),
@@ -335,6 +337,16 @@ def vpl_batch_create(ctx, gbufs, vsets, outs, tile_w: int = 0) -> int:
     bid = C.c_uint64()
     _check(ctx, load().vpl_batch_create(ctx, n, gb, vs, op, int(tile_w), C.byref(bid)), "vpl_batch_create")
     return int(bid.value)
+
+
+def vpl_gather_views(ctx, scene: int, gbufs, vsets, outs, params: W.GatherParams, stream=None) -> None:
+    n = len(gbufs)
+    gb = (vpl_gbuffer * n)(*[g.struct() for g in gbufs])
+    vs = (vpl_vpl_set * n)(*[v.struct() for v in vsets])
+    op = (C.c_void_p * n)(*[_ptr(o) for o in outs])
+    p = make_gather(params)
+    _check(ctx, load().vpl_gather_views(ctx, scene, n, gb, vs, op, C.byref(p), _stream(stream)),
+           "vpl_gather_views")
 
 
 def vpl_batch_destroy(ctx, batch: int) -> None:

@@ -1,0 +1,57 @@
+"""Serving with continuous batching on the GPU: requests over two resident
+scenes, admitted into groups on several streams while others run, give the
+same image as each request rendered alone."""
+import numpy as np
+import pytest
+
+from paper_2203_11484_gb300 import serve as S
+from paper_2203_11484_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def test_served_requests_equal_their_renders_alone():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11484_gb300 import build, vpl as V
+    build.build_library()
+    ctx = V.Context(0)
+    try:
+        tiny = W.cornell_workload()
+        room, lo, hi = W.room200k_scene()
+        sids = {"tiny": ctx.upload(tiny.scene), "room": ctx.upload(room)}
+        n_tris = {"tiny": tiny.scene.n_tris, "room": room.n_tris}
+        rng = np.random.default_rng(8)
+        reqs = []
+        base = tiny.views[0]
+        for k, ((w, h), m) in enumerate([((64, 48), 256), ((128, 128), 96), ((80, 80), 512), ((32, 96), 64)]):
+            cam = W.Camera(base.camera.eye, base.camera.forward, base.camera.up, 60.0, w, h)
+            mc, mf = W.split_budget(m, 0.75)
+            gen = W.GenParams(**{**base.gen.__dict__, "m_close": mc, "m_far": mf, "seed": 50 + k})
+            reqs.append(S.Request(len(reqs), "tiny", W.View(cam, gen, base.gather), 0.0))
+        room_reqs = S.random_requests(rng, {"room": (room, lo, hi, W.ROOM_D_CLOSE)}, 6, rate=200.0,
+                                      resolutions=((128, 128), (256, 144), (96, 200)), m_range=(500, 3000))
+        for r in room_reqs:
+            r.rid = len(reqs)
+            reqs.append(r)
+        srv = S.Server(S.GpuBackend(ctx.h, sids, lanes=3), n_tris, lanes=3, max_group=4,
+                       reserve_bytes=256 << 20)
+        stats = srv.run(reqs)
+        torch.cuda.synchronize()
+        assert V.vpl_sync(ctx.h, check=False) == 0
+        assert stats["requests"] == len(reqs)
+        assert srv.groups_launched < len(reqs)       # requests were batched
+        assert srv.max_concurrent_groups >= 2        # groups overlapped
+        lit = 0
+        for r in reqs:
+            c = r.view.camera
+            alone = torch.zeros((c.width * c.height, 4), dtype=torch.float32, device="cuda")
+            V.vpl_render(ctx.h, sids[r.scene], c, r.view.gen, r.view.gather, alone)
+            assert V.vpl_sync(ctx.h, check=False) == 0
+            assert torch.equal(alone, r.image), r.rid
+            lit += float(alone.max()) > 0
+        assert lit >= len(reqs) - 2       # a view may see no indirect light at all
+    finally:
+        ctx.close()
