@@ -48,6 +48,28 @@ def _dist():
     return ws, rank, local
 
 
+# ---- multi-GPU: independent replicas (no collective on the data path) --------
+def replica_seed(base: int, rank: int) -> int:
+    """Each rank renders its own close-up view of its own scene copy."""
+    return base + rank
+
+
+def max_over_ranks(value: float, device) -> float:
+    """The slowest rank's time (the only collective of a run)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job units per second: every rank did `steps` steps in at most max_ms."""
+    return units_per_step * steps * world / (max_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -308,10 +330,10 @@ def run_ours(args):
     # each rank renders its own close-up view
     if args.workload == "clutter1m":
         wl = W.room1m_workload(width=args.width or 1920, height=args.height or 1080, m_total=args.vpls or 32768,
-                               precision=prec, seed=4 + rank)
+                               precision=prec, seed=replica_seed(4, rank))
     else:
         wl = W.room200k_workload(width=args.width or 1024, height=args.height or 1024,
-                                 m_total=args.vpls or 4096, precision=prec, seed=1 + rank)
+                                 m_total=args.vpls or 4096, precision=prec, seed=replica_seed(1, rank))
     view = wl.views[0]
     cam, gen, gat = view.camera, view.gen, view.gather
     M = gen.m_close + gen.m_far
@@ -382,15 +404,10 @@ def run_ours(args):
         raise RuntimeError(f"device status {rc}: {V.vpl_last_error(ctx.h)}")
     step_ms = [a.elapsed_time(b) for a, b in ev]
     gather_ms = [a.elapsed_time(b) for a, b in gev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), "cuda")
     for s in sids:
         V.vpl_scene_release(ctx.h, s)
-    value = units * args.steps * ws / (total_ms / 1e3)
+    value = job_throughput(units, args.steps, ws, total_ms)
 
     # ---- gather roofline: work counters of the last step's inputs (untimed) --
     sid = V.vpl_scene_upload(ctx.h, verts, tris, alb, sc.light, stream)

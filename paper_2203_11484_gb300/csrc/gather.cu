@@ -163,9 +163,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
         float ax = 0.0f, ay = 0.0f, az = 0.0f; // running sums
         float cx = 0.0f, cy_ = 0.0f, cz = 0.0f; // Kahan compensation
         for (int base = 0; base < M; base += 32) {
-            // a latched device error (e.g. a traversal limit) ends the launch early
+            // a BVH walk that hit its limit ends the launch early (the method's
+            // own degenerate cases, such as an empty close range, do not)
             int st = lane == 0 ? *(volatile int *)status : 0;
-            if (__shfl_sync(kFull, st, 0) != 0) break;
+            if (__shfl_sync(kFull, st, 0) == VPL_ERR_TRAVERSAL_LIMIT) break;
             const int i = base + lane;
             if (i < M) {
                 const float4 vp = __ldg(v_pos + i);
