@@ -123,6 +123,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic(workload: str, precision: str):
+    """DRAM bytes per gather launch from the committed ncu summary, valid only
+    while the kernel sources are the ones that were measured (else None)."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in ("gather.cu", "vpl_device.cuh", "build.cu"):
+        with open(os.path.join(ROOT, "paper_2203_11484_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    try:
+        with open(os.path.join(ROOT, "profiles", "gather_room200k_1024x1024_4096vpl_dram.md")) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    if f"source_sha256: {h.hexdigest()}" not in text or f"workload: {workload} {precision}" not in text:
+        return None
+    m = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    return int(m.group(1)) if m else None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -424,7 +444,8 @@ def run_ours(args):
     peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
     achieved = flops / (gather_in_step_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": measured_traffic(wl.name, args.precision),
+                "traffic_note": "DRAM bytes per launch (ncu, profiles/); the working set is L2-resident",
                 "kernel": f"gather_kernel<BVH,{args.precision}>",
                 "peak_note": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz",
                 "counters": {"pairs": cnt[0], "shadow_rays": cnt[1], "node_visits": cnt[2],
