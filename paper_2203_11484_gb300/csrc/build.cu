@@ -1,6 +1,8 @@
 // Scene upload kernels: per-triangle preparation, device prefix sums, a
-// stable LSD radix sort and the linear BVH (Karras 2012 hierarchy over
-// 63-bit Morton codes, bounding boxes fitted bottom-up).  The BVH is not part
+// stable LSD radix sort over 63-bit Morton codes and the BVH: a binary
+// hierarchy by locally-ordered clustering of the Morton-ordered triangles
+// (the Karras 2012 linear hierarchy with boxes fitted bottom-up is the
+// fallback and a build option), collapsed into 4-wide nodes.  The BVH is not part
 // of the paper; it is the acceleration structure behind every ray query of
 // the method (G-buffer, light paths, Eq. 2 and Eq. 1 visibility).
 #include "vpl_internal.h"
@@ -414,6 +416,190 @@ __global__ void bounds_kernel(int n, const int *child, const int *parent_int, co
     }
 }
 
+// ==========================================================================
+// binary hierarchy by parallel locally-ordered clustering (Meister and
+// Bittner 2018): clusters in Morton order, each finds the cluster within +-R
+// positions whose union box has the smallest surface area; mutual nearest
+// neighbours merge; the survivors are compacted in order; repeat until one
+// cluster is left.  Internal nodes are numbered downwards from T-2, so the
+// last merge -- the root -- is node 0.
+// ==========================================================================
+constexpr int kPlocR = 16;
+constexpr int kPlocThreads = 256;
+
+struct PlocCtl {
+    int n_cur;     // clusters left
+    int node_next; // internal nodes made so far
+};
+
+__device__ __forceinline__ float union_area(const float *a, const float *b)
+{
+    const float dx = fmaxf(a[3], b[3]) - fminf(a[0], b[0]);
+    const float dy = fmaxf(a[4], b[4]) - fminf(a[1], b[1]);
+    const float dz = fmaxf(a[5], b[5]) - fminf(a[2], b[2]);
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void ploc_init_kernel(int n, const float *leafbox, int *cref, float *cbox, int *parent_int, PlocCtl *ctl)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        ctl->n_cur = n;
+        ctl->node_next = 0;
+    }
+    if (i < n - 1) parent_int[i] = -1;
+    if (i >= n) return;
+    cref[i] = ~i;
+    for (int a = 0; a < 6; a++) cbox[6 * (int64_t)i + a] = leafbox[6 * (int64_t)i + a];
+}
+
+__global__ void __launch_bounds__(kPlocThreads) ploc_nn_kernel(const PlocCtl *ctl, const float *cbox, int *nn)
+{
+    __shared__ float tile[(kPlocThreads + 2 * kPlocR) * 6];
+    const int n = ctl->n_cur;
+    const int base = blockIdx.x * kPlocThreads;
+    if (n <= 1 || base >= n) return;
+    const int lo = base - kPlocR;
+    for (int k = threadIdx.x; k < kPlocThreads + 2 * kPlocR; k += kPlocThreads) {
+        const int c = lo + k;
+        for (int a = 0; a < 6; a++) tile[6 * k + a] = (c >= 0 && c < n) ? cbox[6 * (int64_t)c + a] : 0.0f;
+    }
+    __syncthreads();
+    const int i = base + threadIdx.x;
+    if (i >= n) return;
+    const float *bi = tile + 6 * (threadIdx.x + kPlocR);
+    const int j0 = max(0, i - kPlocR), j1 = min(n - 1, i + kPlocR);
+    // j ascends and only a strictly smaller area replaces: ties keep the lower
+    // index, so the lowest cluster of the globally smallest pair always finds
+    // a mutual partner and every pass merges at least once
+    int bj = j0 == i ? i + 1 : j0;
+    float best = union_area(bi, tile + 6 * (bj - lo));
+    for (int j = bj + 1; j <= j1; j++) {
+        if (j == i) continue;
+        const float a = union_area(bi, tile + 6 * (j - lo));
+        if (a < best) {
+            best = a;
+            bj = j;
+        }
+    }
+    nn[i] = bj;
+}
+
+// flags packed as keep << 32 | make: one scan gives both prefix sums
+__global__ void ploc_flags_kernel(const PlocCtl *ctl, const int *nn, unsigned long long *flags)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = ctl->n_cur;
+    if (i >= n) return;
+    const int j = n > 1 ? nn[i] : -1;
+    const bool mutual = j >= 0 && nn[j] == i;
+    const bool make = mutual && i < j, keep = !(mutual && i > j);
+    flags[i] = ((unsigned long long)(keep ? 1u : 0u) << 32) | (make ? 1u : 0u);
+}
+
+__global__ void ploc_merge_kernel(int T, const PlocCtl *ctl, const int *nn, const unsigned long long *flags,
+                                  const unsigned long long *off, const int *cref_in, const float *cbox_in,
+                                  int *cref_out, float *cbox_out, int *child, float *nodebox, int *parent_int,
+                                  int *parent_leaf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = ctl->n_cur;
+    if (i >= n) return;
+    const unsigned long long f = flags[i];
+    if (!(f >> 32)) return; // merged into a lower cluster
+    const int pos = (int)(off[i] >> 32);
+    if (f & 1ull) {
+        const int j = nn[i];
+        const int id = (T - 2) - (ctl->node_next + (int)(off[i] & 0xffffffffull));
+        const int a = cref_in[i], b = cref_in[j];
+        child[2 * (int64_t)id] = a;
+        child[2 * (int64_t)id + 1] = b;
+        if (a < 0) parent_leaf[~a] = id; else parent_int[a] = id;
+        if (b < 0) parent_leaf[~b] = id; else parent_int[b] = id;
+        const float *p = cbox_in + 6 * (int64_t)i, *q = cbox_in + 6 * (int64_t)j;
+        float *o = nodebox + 6 * (int64_t)id, *c = cbox_out + 6 * (int64_t)pos;
+        for (int k = 0; k < 3; k++) {
+            o[k] = c[k] = fminf(p[k], q[k]);
+            o[3 + k] = c[3 + k] = fmaxf(p[3 + k], q[3 + k]);
+        }
+        cref_out[pos] = id;
+    } else {
+        cref_out[pos] = cref_in[i];
+        for (int k = 0; k < 6; k++) cbox_out[6 * (int64_t)pos + k] = cbox_in[6 * (int64_t)i + k];
+    }
+}
+
+__global__ void ploc_ctl_kernel(PlocCtl *ctl, const unsigned long long *off)
+{
+    const unsigned long long tot = off[ctl->n_cur];
+    ctl->node_next += (int)(tot & 0xffffffffull);
+    ctl->n_cur = (int)(tot >> 32);
+}
+
+// Runs merge passes until one cluster is left; *done stays false if a check
+// sees no merge over a whole batch of passes (only non-finite boxes can do
+// that), and the caller then builds the Karras hierarchy instead.
+static cudaError_t ploc_build(const Exec &ex, int T, const float *leafbox, int *child, float *nodebox,
+                              int *parent_int, int *parent_leaf, bool *done)
+{
+    const int B = kPlocThreads, kBatch = 8;
+    *done = false;
+    Tmp cref[2], cbox[2], nn, flags, off, ctl;
+    for (int k = 0; k < 2; k++) {
+        VPL_TRY(cref[k].alloc(ex, sizeof(int) * T));
+        VPL_TRY(cbox[k].alloc(ex, sizeof(float) * 6 * T));
+    }
+    VPL_TRY(nn.alloc(ex, sizeof(int) * T));
+    VPL_TRY(flags.alloc(ex, sizeof(unsigned long long) * T));
+    VPL_TRY(off.alloc(ex, sizeof(unsigned long long) * (T + 1)));
+    VPL_TRY(ctl.alloc(ex, sizeof(PlocCtl)));
+    PlocCtl *c = ctl.as<PlocCtl>();
+    ploc_init_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(T, leafbox, cref[0].as<int>(), cbox[0].as<float>(),
+                                                           parent_int, c);
+    VPL_LAUNCHED(ex);
+    int cur = 0, left = T;
+    while (left > 1) {
+        for (int it = 0; it < kBatch; it++) {
+            ploc_nn_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(c, cbox[cur].as<float>(), nn.as<int>());
+            VPL_LAUNCHED(ex);
+            ploc_flags_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(c, nn.as<int>(), flags.as<unsigned long long>());
+            VPL_LAUNCHED(ex);
+            VPL_TRY(exclusive_scan<unsigned long long>(ex, flags.as<unsigned long long>(),
+                                                       off.as<unsigned long long>(), &c->n_cur, T));
+            ploc_merge_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(
+                T, c, nn.as<int>(), flags.as<unsigned long long>(), off.as<unsigned long long>(), cref[cur].as<int>(),
+                cbox[cur].as<float>(), cref[1 - cur].as<int>(), cbox[1 - cur].as<float>(), child, nodebox,
+                parent_int, parent_leaf);
+            VPL_LAUNCHED(ex);
+            ploc_ctl_kernel<<<1, 1, 0, ex.stream>>>(c, off.as<unsigned long long>());
+            VPL_LAUNCHED(ex);
+            cur = 1 - cur;
+        }
+        int now = 0;
+        VPL_TRY(cudaMemcpyAsync(&now, &c->n_cur, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
+        VPL_TRY(cudaStreamSynchronize(ex.stream));
+        if (now >= left) return cudaSuccess; // no progress
+        left = now;
+    }
+    *done = true;
+    return cudaSuccess;
+}
+
+static cudaError_t lbvh_build(const Exec &ex, const uint64_t *keys, int n, const float *leafbox, int *child,
+                              float *nodebox, int *parent_int, int *parent_leaf)
+{
+    const int B = 256;
+    Tmp visits;
+    VPL_TRY(visits.alloc(ex, sizeof(int) * (n - 1)));
+    VPL_TRY(cudaMemsetAsync(visits.p, 0, sizeof(int) * (n - 1), ex.stream));
+    karras_kernel<<<grid_for(n - 1, B), B, 0, ex.stream>>>(keys, n, child, parent_int, parent_leaf);
+    VPL_LAUNCHED(ex);
+    bounds_kernel<<<grid_for(n, B), B, 0, ex.stream>>>(n, child, parent_int, parent_leaf, leafbox, nodebox,
+                                                       visits.as<int>(), ex.status);
+    VPL_LAUNCHED(ex);
+    return cudaSuccess;
+}
+
 // 4-wide nodes: every binary internal node at even depth becomes one node;
 // its children are its own children where those are leaves, else its
 // grandchildren.  Node index = rank among the even-depth internal nodes in
@@ -534,7 +720,7 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
     sb->bytes = bytes;
     VPL_TRY(cudaMemcpyAsync(sb->verts, verts, sizeof(float) * 3 * n_verts, cudaMemcpyDefault, ex.stream));
     VPL_TRY(cudaMemcpyAsync(sb->idx, tris, sizeof(int32_t) * 3 * T, cudaMemcpyDefault, ex.stream));
-    Tmp alb, bk, keys, vals, leafbox, nodebox, child, pint, pleaf, visits;
+    Tmp alb, bk, keys, vals, leafbox, nodebox, child, pint, pleaf;
     VPL_TRY(alb.alloc(ex, sizeof(float) * 3 * T));
     VPL_TRY(cudaMemcpyAsync(alb.p, albedo, sizeof(float) * 3 * T, cudaMemcpyDefault, ex.stream));
     VPL_TRY(bk.alloc(ex, sizeof(BoxKeys)));
@@ -569,15 +755,14 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
     } else {
         VPL_TRY(nodebox.alloc(ex, sizeof(float) * 6 * (T - 1)));
         VPL_TRY(child.alloc(ex, sizeof(int) * 2 * (T - 1)));
-        VPL_TRY(visits.alloc(ex, sizeof(int) * (T - 1)));
-        VPL_TRY(cudaMemsetAsync(visits.p, 0, sizeof(int) * (T - 1), ex.stream));
-        karras_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(keys.as<uint64_t>(), n, child.as<int>(), pint.as<int>(),
-                                                               pleaf.as<int>());
-        VPL_LAUNCHED(ex);
-        bounds_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(n, child.as<int>(), pint.as<int>(), pleaf.as<int>(),
-                                                           leafbox.as<float>(), nodebox.as<float>(), visits.as<int>(),
-                                                           ex.status);
-        VPL_LAUNCHED(ex);
+        bool built = false;
+#if !VPL_BVH_LBVH
+        VPL_TRY(ploc_build(ex, n, leafbox.as<float>(), child.as<int>(), nodebox.as<float>(), pint.as<int>(),
+                           pleaf.as<int>(), &built));
+#endif
+        if (!built)
+            VPL_TRY(lbvh_build(ex, keys.as<uint64_t>(), n, leafbox.as<float>(), child.as<int>(), nodebox.as<float>(),
+                               pint.as<int>(), pleaf.as<int>()));
         Tmp even, idx4;
         VPL_TRY(even.alloc(ex, sizeof(uint32_t) * (T - 1)));
         VPL_TRY(idx4.alloc(ex, sizeof(uint32_t) * T));
