@@ -454,6 +454,29 @@ def run_ours(args):
                 "gather_ms": gather_in_step_ms,
                 "flops_per_unit": {"pair": FLOPS_PER_PAIR, "ray": FLOPS_PER_RAY, "node": FLOPS_PER_NODE,
                                    "tri": FLOPS_PER_TRI}}
+    # ---- shading-only probe: the same launch with V = 1 (no shadow rays) ----
+    # isolates the Eq. 1 arithmetic from the BVH walks; not part of the metric
+    import dataclasses
+    gat_v1 = dataclasses.replace(gat, visibility=W.VIS_NONE)
+    probe_ms = []
+    for k in range(4):
+        flush.fill_(float(k))
+        e0, e1 = mk(), mk()
+        e0.record(stream)
+        V.vpl_gather(ctx.h, sid, gb, vs, gat_v1, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            probe_ms.append(e0.elapsed_time(e1))
+    V.vpl_sync(ctx.h, stream)
+    v1_ms = statistics.mean(probe_ms)
+    v1_tflops = cnt[0] * FLOPS_PER_PAIR / (v1_ms / 1e3) / 1e12
+    med_mhz = clk.get("sm_mhz") or max_mhz
+    roofline["shading_only"] = {
+        "visibility": "none (V = 1)", "gather_ms": v1_ms, "pairs_per_s": cnt[0] / (v1_ms / 1e3),
+        "achieved": v1_tflops, "frac": v1_tflops / peak_tflops,
+        "frac_at_median_clock": v1_tflops / (sms * 128 * 2 * med_mhz * 1e6 / 1e12)}
+    roofline["frac_at_median_clock"] = achieved / (sms * 128 * 2 * med_mhz * 1e6 / 1e12)
     V.vpl_scene_release(ctx.h, sid)
 
     # ---- end to end: host buffers in, image out, through the same API -----

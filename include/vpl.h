@@ -180,7 +180,10 @@ VPL_API const char *vpl_last_error(const vpl_ctx *ctx);
  *  verts  float[n_verts][3], tris int32[n_tris][3] (indices into verts),
  *  albedo float[n_tris][3] diffuse reflectance per face, light: the emitter.
  *  verts/tris/albedo may be host or device pointers.  Requires n_tris >= 1
- *  and indices in [0, n_verts); returns the new scene's id in *out. */
+ *  and indices in [0, n_verts); returns the new scene's id in *out.
+ *  Unlike the other calls it waits on `stream` a few times while the BVH is
+ *  built (the host reads the cluster count back), so it returns after the
+ *  build, and it must not be called while `stream` is being captured. */
 VPL_API int vpl_scene_upload(vpl_ctx *ctx, const float *verts, int64_t n_verts, const int32_t *tris,
                      int64_t n_tris, const float *albedo, const vpl_light *light,
                      vpl_stream stream, vpl_scene_id *out);

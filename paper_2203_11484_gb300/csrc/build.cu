@@ -424,7 +424,10 @@ __global__ void bounds_kernel(int n, const int *child, const int *parent_int, co
 // cluster is left.  Internal nodes are numbered downwards from T-2, so the
 // last merge -- the root -- is node 0.
 // ==========================================================================
-constexpr int kPlocR = 16;
+#ifndef VPL_PLOC_R
+#define VPL_PLOC_R 32
+#endif
+constexpr int kPlocR = VPL_PLOC_R; // neighbour search radius
 constexpr int kPlocThreads = 256;
 
 struct PlocCtl {
@@ -627,6 +630,8 @@ __device__ __forceinline__ void put_child(float lo[3][4], float hi[3][4], int *r
     cnt[m] = c;
 }
 
+__device__ __forceinline__ void write_node4(float lo[3][4], float hi[3][4], int *ref, int *cnt, int m, float4 *o);
+
 __global__ void pack4_kernel(int n, const int *child, const float *leafbox, const float *nodebox,
                              const uint32_t *even, const uint32_t *idx4, float4 *nodes)
 {
@@ -646,6 +651,12 @@ __global__ void pack4_kernel(int n, const int *child, const float *leafbox, cons
             else put_child(lo, hi, ref, cnt, m++, (int)idx4[g], 0, nodebox + 6 * (int64_t)g);
         }
     }
+    write_node4(lo, hi, ref, cnt, m, nodes + 8 * (int64_t)idx4[i]);
+}
+
+// pads the m filled slots with empty ones and stores the 128-byte node
+__device__ __forceinline__ void write_node4(float lo[3][4], float hi[3][4], int *ref, int *cnt, int m, float4 *o)
+{
     // empty slots: a point box at (3e38, -3e38, 3e38), which no segment or ray
     // of a scene reaches
     const float farbox[6] = {3.0e38f, -3.0e38f, 3.0e38f, 3.0e38f, -3.0e38f, 3.0e38f};
@@ -655,7 +666,6 @@ __global__ void pack4_kernel(int n, const int *child, const float *leafbox, cons
         if (ref[k] < 0 && ref[k] != kEmptyRef) leafmask |= 1u << k;
         packed |= (unsigned)(cnt[k] & 255) << (8 * k);
     }
-    float4 *o = nodes + 8 * (int64_t)idx4[i];
     o[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
     o[1] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
     o[2] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
@@ -664,6 +674,101 @@ __global__ void pack4_kernel(int n, const int *child, const float *leafbox, cons
     o[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
     o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
     o[7] = make_float4(__uint_as_float(leafmask), __uint_as_float(packed), 0.0f, 0.0f);
+}
+
+// 4-wide nodes by surface area, top down one level per launch: a node starts
+// from the two children of its binary node and, while it has fewer than four
+// slots, opens the internal slot with the largest box surface into that
+// node's two children.  Internal slots left become the next level's nodes,
+// numbered in allocation order (root 0, then breadth first), so the result
+// does not depend on that order: only the slot contents and their order,
+// fixed by the rule, steer a traversal.
+constexpr int kCollapseLevels = (kStackMax - 1) / 3; // each level pushes <= 3 stack entries
+
+__device__ __forceinline__ float box_area(const float *b)
+{
+    const float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void collapse_init_kernel(int2 *queue, int *count, int *next)
+{
+    queue[0] = make_int2(0, 0);
+    count[0] = 1;
+    for (int l = 1; l <= kCollapseLevels; l++) count[l] = 0;
+    *next = 1;
+}
+
+__global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, int *count, int *next,
+                                      const int *child, const float *leafbox, const float *nodebox, float4 *nodes)
+{
+    const int n_in = count[level];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_in; q += gridDim.x * blockDim.x) {
+        const int2 w = qin[q];
+        int slot[4] = {child[2 * w.x], child[2 * w.x + 1], 0, 0};
+        int m = 2;
+        while (m < 4) {
+            int pick = -1;
+            float best = -1.0f;
+            for (int k = 0; k < m; k++)
+                if (slot[k] >= 0) {
+                    const float a = box_area(nodebox + 6 * (int64_t)slot[k]);
+                    if (pick < 0 || a > best) {
+                        pick = k;
+                        best = a;
+                    }
+                }
+            if (pick < 0) break;
+            const int c = slot[pick];
+            slot[pick] = child[2 * c];
+            slot[m++] = child[2 * c + 1];
+        }
+        int n_int = 0;
+        for (int k = 0; k < m; k++) n_int += slot[k] >= 0;
+        const int base = n_int ? atomicAdd(next, n_int) : 0;
+        const int pos = n_int ? atomicAdd(&count[level + 1], n_int) : 0;
+        float lo[3][4], hi[3][4];
+        int ref[4], cnt[4], j = 0;
+        for (int k = 0; k < m; k++) {
+            const int c = slot[k];
+            if (c < 0) {
+                put_child(lo, hi, ref, cnt, k, c, 1, leafbox + 6 * (int64_t)(~c));
+            } else {
+                put_child(lo, hi, ref, cnt, k, base + j, 0, nodebox + 6 * (int64_t)c);
+                qout[pos + j] = make_int2(c, base + j);
+                j++;
+            }
+        }
+        write_node4(lo, hi, ref, cnt, m, nodes + 8 * (int64_t)w.y);
+    }
+}
+
+// Runs the levels; *done stays false if internal nodes are left after
+// kCollapseLevels levels (a tree too deep for the traversal stack), and the
+// caller then packs by even depth, whose stack use the depth check bounds.
+static cudaError_t collapse_sah(const Exec &ex, int T, const int *child, const float *leafbox, const float *nodebox,
+                                float4 *nodes, bool *done)
+{
+    *done = false;
+    Tmp qa, qb, cnt, next;
+    VPL_TRY(qa.alloc(ex, sizeof(int2) * T));
+    VPL_TRY(qb.alloc(ex, sizeof(int2) * T));
+    VPL_TRY(cnt.alloc(ex, sizeof(int) * (kCollapseLevels + 1)));
+    VPL_TRY(next.alloc(ex, sizeof(int)));
+    collapse_init_kernel<<<1, 1, 0, ex.stream>>>(qa.as<int2>(), cnt.as<int>(), next.as<int>());
+    VPL_LAUNCHED(ex);
+    const unsigned grid = grid_for(T, 256) < 1216u ? grid_for(T, 256) : 1216u;
+    for (int l = 0; l < kCollapseLevels; l++) {
+        const Tmp &in = (l & 1) ? qb : qa, &out = (l & 1) ? qa : qb;
+        collapse_level_kernel<<<grid, 256, 0, ex.stream>>>(l, in.as<int2>(), out.as<int2>(), cnt.as<int>(),
+                                                           next.as<int>(), child, leafbox, nodebox, nodes);
+        VPL_LAUNCHED(ex);
+    }
+    int left = 0;
+    VPL_TRY(cudaMemcpyAsync(&left, cnt.as<int>() + kCollapseLevels, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
+    VPL_TRY(cudaStreamSynchronize(ex.stream));
+    *done = left == 0;
+    return cudaSuccess;
 }
 
 // one triangle: a root with the leaf in slot 0 and three empty slots
@@ -763,16 +868,22 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
         if (!built)
             VPL_TRY(lbvh_build(ex, keys.as<uint64_t>(), n, leafbox.as<float>(), child.as<int>(), nodebox.as<float>(),
                                pint.as<int>(), pleaf.as<int>()));
-        Tmp even, idx4;
-        VPL_TRY(even.alloc(ex, sizeof(uint32_t) * (T - 1)));
-        VPL_TRY(idx4.alloc(ex, sizeof(uint32_t) * T));
-        even_depth_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, pint.as<int>(), even.as<uint32_t>());
-        VPL_LAUNCHED(ex);
-        VPL_TRY(exclusive_scan<uint32_t>(ex, even.as<uint32_t>(), idx4.as<uint32_t>(), nullptr, T - 1));
-        pack4_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, child.as<int>(), leafbox.as<float>(),
-                                                              nodebox.as<float>(), even.as<uint32_t>(),
-                                                              idx4.as<uint32_t>(), sb->nodes);
-        VPL_LAUNCHED(ex);
+        bool packed = false;
+#if !VPL_BVH_EVEN_COLLAPSE
+        VPL_TRY(collapse_sah(ex, n, child.as<int>(), leafbox.as<float>(), nodebox.as<float>(), sb->nodes, &packed));
+#endif
+        if (!packed) {
+            Tmp even, idx4;
+            VPL_TRY(even.alloc(ex, sizeof(uint32_t) * (T - 1)));
+            VPL_TRY(idx4.alloc(ex, sizeof(uint32_t) * T));
+            even_depth_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, pint.as<int>(), even.as<uint32_t>());
+            VPL_LAUNCHED(ex);
+            VPL_TRY(exclusive_scan<uint32_t>(ex, even.as<uint32_t>(), idx4.as<uint32_t>(), nullptr, T - 1));
+            pack4_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, child.as<int>(), leafbox.as<float>(),
+                                                                  nodebox.as<float>(), even.as<uint32_t>(),
+                                                                  idx4.as<uint32_t>(), sb->nodes);
+            VPL_LAUNCHED(ex);
+        }
     }
     depth_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(n, pint.as<int>(), pleaf.as<int>(), sb->depth, ex.status);
     VPL_LAUNCHED(ex);
