@@ -13,8 +13,8 @@
 namespace vpl {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kDepthMax = 96;            // binary LBVH depth, checked when a scene is built
-constexpr int kStackMax = 160;           // >= 3 x depth of the 4-wide tree, (kDepthMax + 1) / 2 + 1
+constexpr int kDepthMax = 96;            // binary hierarchy depth, checked when a scene is built
+constexpr int kStackMax = 160;           // >= 3 x levels of the 4-wide tree (<= 53) + 1
 constexpr int kTraversalLimit = 1 << 16; // node visits per query before giving up
 constexpr float kPi = 3.14159265358979323846f;
 constexpr double kPiD = 3.14159265358979323846;
@@ -26,7 +26,7 @@ struct SceneView {
     int32_t n_tris;
     int32_t n_nodes;
     const float4 *tri;     // 3 per triangle, BVH leaf order: v0 (w = original id bits), e1, e2
-    const float4 *nodes;   // 4 per internal node (see bvh.cu)
+    const float4 *nodes;   // 8 per 4-wide node (see Node4)
     const float4 *nrm;     // per original triangle: unit normal (FP32 from FP64)
     const float4 *rho;     // per original triangle: albedo
     const float *verts;    // original FP32 vertices
@@ -202,6 +202,18 @@ struct Node4 {
     int ref[4], cnt[4];
     unsigned leafmask; // bit k set: child k is a leaf
 };
+
+// child references, leaf mask and leaf triangle counts (rows 6 and 7)
+__device__ __forceinline__ void load_node4_meta(const float4 *p, Node4 &n)
+{
+    float4 r = __ldg(p + 6), c = __ldg(p + 7);
+    n.ref[0] = __float_as_int(r.x); n.ref[1] = __float_as_int(r.y);
+    n.ref[2] = __float_as_int(r.z); n.ref[3] = __float_as_int(r.w);
+    n.leafmask = __float_as_uint(c.x);
+    const unsigned packed = __float_as_uint(c.y); // 8-bit triangle counts of leaf children
+    n.cnt[0] = packed & 255u; n.cnt[1] = (packed >> 8) & 255u;
+    n.cnt[2] = (packed >> 16) & 255u; n.cnt[3] = packed >> 24;
+}
 
 __device__ __forceinline__ void load_node4(const float4 *nodes, int node, Node4 &n)
 {
@@ -436,28 +448,60 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     }
     unsigned alive = __ballot_sync(kFull, want && !occl);
     if (alive == 0) return occl;
+    // Direction signs of the live segments, per axis.  When every live segment
+    // of the packet points the same way along an axis, the entry plane of that
+    // axis is the same box face for all of them, so the packet loads the near
+    // and far rows by address and skips the per-lane min/max that orders the
+    // two plane crossings (the usual case: 32 pixels of a small tile seen from
+    // one VPL).  Otherwise it takes the general slab test.
+    const unsigned nx = __ballot_sync(kFull, want && !occl && signbit(r.inv.x));
+    const unsigned ny = __ballot_sync(kFull, want && !occl && signbit(r.inv.y));
+    const unsigned nz = __ballot_sync(kFull, want && !occl && signbit(r.inv.z));
+    const bool oriented = (nx == 0 || nx == alive) && (ny == 0 || ny == alive) && (nz == 0 || nz == alive);
+    const int fx = nx ? 1 : 0, fy = ny ? 3 : 2, fz = nz ? 5 : 4; // row of each axis' entry plane
     int sp = 0, node = 0, steps = 0;
     const float kInf = __int_as_float(0x7f800000);
     while (true) {
         Node4 n;
-        load_node4(s.nodes, node, n);
         const bool live = want && !occl;
-        const unsigned leafmask = n.leafmask;
         unsigned hits = 0;     // children this lane's segment enters
         int mine = -1;         // the nearest internal one
         float tmine = kInf;
+        if (oriented) {
+            const float4 *p = s.nodes + 8 * (int64_t)node;
+            const float4 ex = __ldg(p + fx), xx = __ldg(p + (fx ^ 1)), ey = __ldg(p + fy), xy = __ldg(p + (fy ^ 1)),
+                         ez = __ldg(p + fz), xz = __ldg(p + (fz ^ 1));
+            load_node4_meta(p, n);
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            float te;
-            // empty slots hold a box no segment of a scene reaches: no test needed
-            if (live && slab(r, n, k, 0.0f, 1.0f, te)) {
-                hits |= 1u << k;
-                if (!((leafmask >> k) & 1u) && te < tmine) {
-                    tmine = te;
-                    mine = k;
+            for (int k = 0; k < 4; k++) {
+                const float te = fmax3(fmaf(comp(ex, k), r.inv.x, -r.oinv.x), fmaf(comp(ey, k), r.inv.y, -r.oinv.y),
+                                       fmaxf(fmaf(comp(ez, k), r.inv.z, -r.oinv.z), 0.0f));
+                const float tx = fmin3(fmaf(comp(xx, k), r.inv.x, -r.oinv.x), fmaf(comp(xy, k), r.inv.y, -r.oinv.y),
+                                       fminf(fmaf(comp(xz, k), r.inv.z, -r.oinv.z), 1.0f));
+                if (live && te <= tx) {
+                    hits |= 1u << k;
+                    if (!((n.leafmask >> k) & 1u) && te < tmine) {
+                        tmine = te;
+                        mine = k;
+                    }
+                }
+            }
+        } else {
+            load_node4(s.nodes, node, n);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                float te;
+                // empty slots hold a box no segment of a scene reaches: no test needed
+                if (live && slab(r, n, k, 0.0f, 1.0f, te)) {
+                    hits |= 1u << k;
+                    if (!((n.leafmask >> k) & 1u) && te < tmine) {
+                        tmine = te;
+                        mine = k;
+                    }
                 }
             }
         }
+        const unsigned leafmask = n.leafmask;
         if (COUNT) {
             wc.steps++;
             if (live) wc.visits++;
