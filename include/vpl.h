@@ -199,7 +199,9 @@ VPL_API int vpl_gbuffer_build(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera
 /* Steps (1)-(3): out->count must equal m_close + m_far. */
 VPL_API int vpl_generate(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam,
                  const vpl_gen_params *gen, const vpl_vpl_set *vpls, vpl_stream stream);
-/* Synchronises the stream of the last vpl_generate and reports its numbers. */
+/* Synchronises the device and reports the numbers of the generation that
+ * finished last (vpl_generate or vpl_render; with calls in flight on several
+ * streams, whichever of them wrote its record last). */
 VPL_API int vpl_generate_info(vpl_ctx *ctx, vpl_gen_info *out);
 
 /* Step (4): out_rgba (device float4[width*height]) receives, per pixel,

@@ -341,10 +341,16 @@ __global__ void far_tail_kernel(GenArgs g, const GenInfoDev *info, float4 *pos, 
 }
 
 cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, float4 *pos, void *nrm,
-                          void *flux, int fmt, GenInfoDev *info)
+                          void *flux, int fmt, GenInfoDev *report)
 {
     const int T = s.n_tris;
     const int TB = kGenThreads;
+    // the kernels below read back what earlier ones wrote here, so each call
+    // has its own record (calls on other streams may run at the same time);
+    // it is copied to `report` at the end
+    Tmp rec;
+    VPL_TRY(rec.alloc(ex, sizeof(GenInfoDev)));
+    GenInfoDev *info = rec.as<GenInfoDev>();
     VPL_TRY(cudaMemsetAsync(info, 0, sizeof(GenInfoDev), ex.stream));
     Tmp flag, fpos;
     VPL_TRY(flag.alloc(ex, sizeof(uint32_t) * T));
@@ -420,6 +426,7 @@ cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, 
         far_tail_kernel<<<grid_for(g.m_far, 256), 256, 0, ex.stream>>>(g, info, pos, nrm, flux, fmt);
         VPL_LAUNCHED(ex);
     }
+    if (report) VPL_TRY(cudaMemcpyAsync(report, info, sizeof(GenInfoDev), cudaMemcpyDeviceToDevice, ex.stream));
     return cudaSuccess;
 }
 

@@ -98,7 +98,7 @@ struct GenInfoDev {
 };
 
 cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, float4 *pos,
-                          void *nrm, void *flux, int format, GenInfoDev *info);
+                          void *nrm, void *flux, int format, GenInfoDev *report);
 
 // ---- gather.cu -----------------------------------------------------------------
 struct CamArgs {

@@ -55,3 +55,41 @@ def test_served_requests_equal_their_renders_alone():
         assert lit >= len(reqs) - 2       # a view may see no indirect light at all
     finally:
         ctx.close()
+
+
+def test_generations_on_two_streams_at_once_match_one_at_a_time():
+    """Each generation keeps its own device record of close-set size, area
+    total and path count, so calls overlapping on two streams of one context
+    give the VPL sets they give alone."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11484_gb300 import build, vpl as V
+    build.build_library()
+    ctx = V.Context(0)
+    try:
+        room, lo, hi = W.room200k_scene()
+        sid = ctx.upload(room)
+        reqs = S.random_requests(np.random.default_rng(21), {"room": (room, lo, hi, W.ROOM_D_CLOSE)}, 6,
+                                 rate=100.0, resolutions=((64, 64),), m_range=(500, 3000))
+        views = [(r.view.camera, r.view.gen) for r in reqs]
+
+        def run(streams):
+            sets = []
+            for k, (cam, gen) in enumerate(views):
+                s = streams[k % len(streams)]
+                with torch.cuda.stream(s):
+                    vs = V.VplSet.empty(gen.m_close + gen.m_far, "cuda")
+                    V.vpl_generate(ctx.h, sid, cam, gen, vs, s)
+                sets.append(vs)
+            torch.cuda.synchronize()
+            return sets
+
+        one = run([torch.cuda.current_stream()])
+        assert V.vpl_sync(ctx.h, check=False) == 0
+        for _ in range(3):
+            two = run([torch.cuda.Stream(), torch.cuda.Stream()])
+            assert V.vpl_sync(ctx.h, check=False) == 0
+            for a, b in zip(one, two):
+                assert torch.equal(a.pos, b.pos) and torch.equal(a.nrm, b.nrm) and torch.equal(a.flux, b.flux)
+    finally:
+        ctx.close()
