@@ -660,6 +660,28 @@ __device__ __forceinline__ void write_node4(float lo[3][4], float hi[3][4], int 
     // empty slots: a point box at (3e38, -3e38, 3e38), which no segment or ray
     // of a scene reaches
     const float farbox[6] = {3.0e38f, -3.0e38f, 3.0e38f, 3.0e38f, -3.0e38f, 3.0e38f};
+    // slots in order of box surface, largest first (the packet shadow walk
+    // visits internal children in slot order)
+    for (int i = 1; i < m; i++)
+        for (int j = i; j > 0; j--) {
+            float aj = 0.0f, ap = 0.0f;
+            {
+                const float dx = hi[0][j] - lo[0][j], dy = hi[1][j] - lo[1][j], dz = hi[2][j] - lo[2][j];
+                aj = dx * dy + dy * dz + dz * dx;
+            }
+            {
+                const float dx = hi[0][j - 1] - lo[0][j - 1], dy = hi[1][j - 1] - lo[1][j - 1],
+                            dz = hi[2][j - 1] - lo[2][j - 1];
+                ap = dx * dy + dy * dz + dz * dx;
+            }
+            if (!(aj > ap)) break;
+            for (int a = 0; a < 3; a++) {
+                float t = lo[a][j]; lo[a][j] = lo[a][j - 1]; lo[a][j - 1] = t;
+                t = hi[a][j]; hi[a][j] = hi[a][j - 1]; hi[a][j - 1] = t;
+            }
+            int t = ref[j]; ref[j] = ref[j - 1]; ref[j - 1] = t;
+            t = cnt[j]; cnt[j] = cnt[j - 1]; cnt[j - 1] = t;
+        }
     while (m < 4) put_child(lo, hi, ref, cnt, m++, kEmptyRef, 0, farbox);
     unsigned leafmask = 0, packed = 0;
     for (int k = 0; k < 4; k++) {

@@ -20,7 +20,7 @@ constexpr int kTileW = 8, kTileH = 4;
 // resident blocks per SM the gather is compiled for (register budget
 // 65536 / (128 * blocks)); a build-time tuning knob
 #ifndef VPL_GATHER_MIN_BLOCKS
-#define VPL_GATHER_MIN_BLOCKS 5
+#define VPL_GATHER_MIN_BLOCKS 7
 #endif
 
 __device__ __forceinline__ float4 load_attr(const void *base, int64_t i, int fmt)
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
         const bool valid = inb && __float_as_int(gp.w) >= 0;
         float4 gn = valid ? load_attr(g_nrm, p, gfmt) : make_float4(0, 0, 0, 0);
         const float3 y = f3(gp), ny = f3(gn);
-        const float3 o = y + ny * eps;
+        const float3 o = fma3(ny, eps, y);
         int occ_cache = -1;                    // last blocking triangle of this pixel
         float ax = 0.0f, ay = 0.0f, az = 0.0f; // running sums
         float cx = 0.0f, cy_ = 0.0f, cz = 0.0f; // Kahan compensation
@@ -191,10 +191,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                 const bool want = valid && lit && cosy > 0.0f && cosi > 0.0f && d2 > 0.0f;
                 bool vis = true;
                 if (VIS == VPL_VIS_BVH) {
-                    const float3 q = f3(xp) + f3(xn) * eps;
+                    const float3 q = fma3(f3(xn), eps, f3(xp));
                     vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), occ_cache, stack[wid], status, wc);
                 } else if (VIS == VPL_VIS_BRUTE) {
-                    const float3 q = f3(xp) + f3(xn) * eps;
+                    const float3 q = fma3(f3(xn), eps, f3(xp));
                     vis = !warp_occluded_brute<COUNT>(s, want, make_ray(o, q - o), wc);
                 }
                 if (COUNT) {

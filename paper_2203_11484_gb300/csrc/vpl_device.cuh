@@ -45,16 +45,34 @@ __device__ __forceinline__ void latch(int *status, int code)
 }
 
 // --------------------------------------------------------------------------
-// FP32 vectors
+// FP32 vectors.  Every operation has its rounding spelled out (fmaf where a
+// product feeds a sum), so the compiler cannot fuse differently in the
+// several instantiations of a kernel: a segment's visibility and a pair's
+// shading terms come out bit for bit the same in every gather variant.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
-__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
-__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b)
+{
+    return make_float3(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z));
+}
+__device__ __forceinline__ float3 operator-(float3 a, float3 b)
+{
+    return make_float3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+__device__ __forceinline__ float3 operator*(float3 a, float s)
+{
+    return make_float3(__fmul_rn(a.x, s), __fmul_rn(a.y, s), __fmul_rn(a.z, s));
+}
+// a * s + b with one rounding per component
+__device__ __forceinline__ float3 fma3(float3 a, float s, float3 b)
+{
+    return make_float3(fmaf(a.x, s, b.x), fmaf(a.y, s, b.y), fmaf(a.z, s, b.z));
+}
+__device__ __forceinline__ float dot(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, __fmul_rn(a.z, b.z))); }
 __device__ __forceinline__ float3 cross(float3 a, float3 b)
 {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    return make_float3(fmaf(a.y, b.z, -__fmul_rn(a.z, b.y)), fmaf(a.z, b.x, -__fmul_rn(a.x, b.z)),
+                       fmaf(a.x, b.y, -__fmul_rn(a.y, b.x)));
 }
 
 // --------------------------------------------------------------------------
@@ -181,12 +199,12 @@ __device__ __forceinline__ bool tri_hit(const Ray &r, float4 v0, float4 e1v, flo
     if (det == 0.0f) return false;
     float inv = 1.0f / det;
     float3 tv = r.o - f3(v0);
-    float u = dot(tv, pv) * inv;
+    float u = __fmul_rn(dot(tv, pv), inv);
     if (u < 0.0f || u > 1.0f) return false;
     float3 qv = cross(tv, e1);
-    float v = dot(r.d, qv) * inv;
-    if (v < 0.0f || u + v > 1.0f) return false;
-    t = dot(e2, qv) * inv;
+    float v = __fmul_rn(dot(r.d, qv), inv);
+    if (v < 0.0f || __fadd_rn(u, v) > 1.0f) return false;
+    t = __fmul_rn(dot(e2, qv), inv);
     return true;
 }
 
@@ -243,6 +261,25 @@ __device__ __forceinline__ float fmax3(float a, float b, float c)
 {
     float r;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// two FP32 FMAs in one instruction (f32x2, sm_100 and later); each lane is an
+// ordinary round-to-nearest fma, so results equal fmaf element by element
+__device__ __forceinline__ unsigned long long pack2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float4 fma4(const float4 &v, unsigned long long s2, unsigned long long c2)
+{
+    unsigned long long lo, hi;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(lo) : "l"(pack2(v.x, v.y)), "l"(s2), "l"(c2));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(hi) : "l"(pack2(v.z, v.w)), "l"(s2), "l"(c2));
+    float4 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(lo));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.z), "=f"(r.w) : "l"(hi));
     return r;
 }
 
@@ -402,9 +439,11 @@ __device__ __forceinline__ bool occluded_brute(const SceneView &s, const Ray &r)
 // the same address in every lane (one transaction, broadcast).  Per node each
 // lane forms a 4-bit mask of the children its segment enters; one OR-reduction
 // over the warp gives the children any lane needs.  Leaf children are tested
-// at once; among internal children the packet descends into the one the first
-// live lane enters first and pushes the others on a warp-uniform stack in
-// shared memory (`stk`, kStackMax entries per warp).
+// at once; among internal children the packet visits them in slot order (the
+// builder puts the largest box first): it descends into the first and pushes
+// the others on a warp-uniform stack in shared memory (`stk`, kStackMax
+// entries per warp) with the next slot on top.  A distance-ordered descent
+// saves a few node visits but costs more than it saves in per-node work.
 // --------------------------------------------------------------------------
 struct WarpCounters {
     uint32_t visits, tests; // per lane: nodes visited / triangles tested by its own ray
@@ -459,32 +498,26 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     const unsigned nz = __ballot_sync(kFull, want && !occl && signbit(r.inv.z));
     const bool oriented = (nx == 0 || nx == alive) && (ny == 0 || ny == alive) && (nz == 0 || nz == alive);
     const int fx = nx ? 1 : 0, fy = ny ? 3 : 2, fz = nz ? 5 : 4; // row of each axis' entry plane
+    const unsigned long long sx2 = pack2(r.inv.x, r.inv.x), cx2 = pack2(-r.oinv.x, -r.oinv.x);
+    const unsigned long long sy2 = pack2(r.inv.y, r.inv.y), cy2 = pack2(-r.oinv.y, -r.oinv.y);
+    const unsigned long long sz2 = pack2(r.inv.z, r.inv.z), cz2 = pack2(-r.oinv.z, -r.oinv.z);
     int sp = 0, node = 0, steps = 0;
-    const float kInf = __int_as_float(0x7f800000);
     while (true) {
         Node4 n;
         const bool live = want && !occl;
         unsigned hits = 0;     // children this lane's segment enters
-        int mine = -1;         // the nearest internal one
-        float tmine = kInf;
         if (oriented) {
             const float4 *p = s.nodes + 8 * (int64_t)node;
-            const float4 ex = __ldg(p + fx), xx = __ldg(p + (fx ^ 1)), ey = __ldg(p + fy), xy = __ldg(p + (fy ^ 1)),
-                         ez = __ldg(p + fz), xz = __ldg(p + (fz ^ 1));
+            // plane crossings of all four children, two per instruction
+            const float4 ex = fma4(__ldg(p + fx), sx2, cx2), xx = fma4(__ldg(p + (fx ^ 1)), sx2, cx2);
+            const float4 ey = fma4(__ldg(p + fy), sy2, cy2), xy = fma4(__ldg(p + (fy ^ 1)), sy2, cy2);
+            const float4 ez = fma4(__ldg(p + fz), sz2, cz2), xz = fma4(__ldg(p + (fz ^ 1)), sz2, cz2);
             load_node4_meta(p, n);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const float te = fmax3(fmaf(comp(ex, k), r.inv.x, -r.oinv.x), fmaf(comp(ey, k), r.inv.y, -r.oinv.y),
-                                       fmaxf(fmaf(comp(ez, k), r.inv.z, -r.oinv.z), 0.0f));
-                const float tx = fmin3(fmaf(comp(xx, k), r.inv.x, -r.oinv.x), fmaf(comp(xy, k), r.inv.y, -r.oinv.y),
-                                       fminf(fmaf(comp(xz, k), r.inv.z, -r.oinv.z), 1.0f));
-                if (live && te <= tx) {
-                    hits |= 1u << k;
-                    if (!((n.leafmask >> k) & 1u) && te < tmine) {
-                        tmine = te;
-                        mine = k;
-                    }
-                }
+                const float te = fmax3(comp(ex, k), comp(ey, k), fmaxf(comp(ez, k), 0.0f));
+                const float tx = fmin3(comp(xx, k), comp(xy, k), fminf(comp(xz, k), 1.0f));
+                if (live && te <= tx) hits |= 1u << k;
             }
         } else {
             load_node4(s.nodes, node, n);
@@ -492,13 +525,7 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
             for (int k = 0; k < 4; k++) {
                 float te;
                 // empty slots hold a box no segment of a scene reaches: no test needed
-                if (live && slab(r, n, k, 0.0f, 1.0f, te)) {
-                    hits |= 1u << k;
-                    if (!((n.leafmask >> k) & 1u) && te < tmine) {
-                        tmine = te;
-                        mine = k;
-                    }
-                }
+                if (live && slab(r, n, k, 0.0f, 1.0f, te)) hits |= 1u << k;
             }
         }
         const unsigned leafmask = n.leafmask;
@@ -518,18 +545,15 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
         }
         unsigned need = any & ~leafmask;
         if (need) {
-            // descend where the first live lane goes first (else the lowest child needed)
-            const int leader = __ffs(__ballot_sync(kFull, want && !occl)) - 1;
-            int pick = __shfl_sync(kFull, occl ? -1 : mine, leader);
-            if (pick < 0) pick = __ffs(need) - 1;
-            need &= ~(1u << pick);
+            const int pick = __ffs(need) - 1;
+            need &= need - 1;
             if (sp + __popc(need) > kStackMax) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
-            while (need) {
-                int k = __ffs(need) - 1;
-                need &= need - 1;
-                if (lane == 0) stk[sp] = k == 0 ? n.ref[0] : k == 1 ? n.ref[1] : k == 2 ? n.ref[2] : n.ref[3];
-                sp++;
-            }
+            // lanes 0-3 push the other children at once, lowest slot on top
+            const int mk = lane & 3;
+            if (lane < 4 && ((need >> mk) & 1u))
+                stk[sp + __popc(need >> (mk + 1))] =
+                    mk == 0 ? n.ref[0] : mk == 1 ? n.ref[1] : mk == 2 ? n.ref[2] : n.ref[3];
+            sp += __popc(need);
             node = pick == 0 ? n.ref[0] : pick == 1 ? n.ref[1] : pick == 2 ? n.ref[2] : n.ref[3];
         } else {
             if (sp == 0) break;
