@@ -439,7 +439,8 @@ __device__ __forceinline__ bool occluded_brute(const SceneView &s, const Ray &r)
 // the same address in every lane (one transaction, broadcast).  Per node each
 // lane forms a 4-bit mask of the children its segment enters; one OR-reduction
 // over the warp gives the children any lane needs.  Leaf children are tested
-// at once; among internal children the packet visits them in slot order (the
+// at once, each lane its own (divergent loads, one leaf per lane and round);
+// among internal children the packet visits them in slot order (the
 // builder puts the largest box first): it descends into the first and pushes
 // the others on a warp-uniform stack in shared memory (`stk`, kStackMax
 // entries per warp) with the next slot on top.  A distance-ordered descent
@@ -449,23 +450,6 @@ struct WarpCounters {
     uint32_t visits, tests; // per lane: nodes visited / triangles tested by its own ray
     uint32_t steps;         // per warp: packet traversal steps (same in every lane)
 };
-
-template <bool COUNT>
-__device__ __forceinline__ void leaf_any(const SceneView &s, const Ray &r, int first, int cnt,
-                                         bool mask, bool &occl, int &cache, WarpCounters &wc)
-{
-    for (int k = first; k < first + cnt; k++) {
-        float4 v0 = __ldg(s.tri + 3 * k), e1 = __ldg(s.tri + 3 * k + 1), e2 = __ldg(s.tri + 3 * k + 2);
-        if (mask && !occl) {
-            float t;
-            if (COUNT) wc.tests++;
-            if (tri_hit(r, v0, e1, e2, t) && t > 0.0f && t < 1.0f) {
-                occl = true;
-                cache = k;
-            }
-        }
-    }
-}
 
 // `cache` (per lane) is the leaf-order slot of the triangle that last blocked
 // one of this lane's segments, or -1.  It is tested before the traversal:
@@ -535,10 +519,27 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
         }
         unsigned any = __reduce_or_sync(kFull, hits);
         if (any & leafmask) {
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if ((any & leafmask) >> k & 1u)
-                    leaf_any<COUNT>(s, r, ~n.ref[k], n.cnt[k], (hits >> k) & 1u, occl, cache, wc);
+            // each lane tests the leaves its own segment enters, one per
+            // round: the rounds are the most leaves any one lane enters,
+            // not all the leaves any lane enters
+            unsigned todo = hits & leafmask;
+            while (__any_sync(kFull, todo != 0 && !occl)) {
+                if (todo != 0 && !occl) {
+                    const int k = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int first = ~(k == 0 ? n.ref[0] : k == 1 ? n.ref[1] : k == 2 ? n.ref[2] : n.ref[3]);
+                    const int c = k == 0 ? n.cnt[0] : k == 1 ? n.cnt[1] : k == 2 ? n.cnt[2] : n.cnt[3];
+                    for (int q = first; q < first + c && !occl; q++) {
+                        float t;
+                        if (COUNT) wc.tests++;
+                        if (tri_hit(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2), t) &&
+                            t > 0.0f && t < 1.0f) {
+                            occl = true;
+                            cache = q;
+                        }
+                    }
+                }
+            }
             alive = __ballot_sync(kFull, want && !occl);
             if (alive == 0) break;
             any = __reduce_or_sync(kFull, occl ? 0u : hits);
