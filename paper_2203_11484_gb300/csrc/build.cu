@@ -603,108 +603,21 @@ static cudaError_t lbvh_build(const Exec &ex, const uint64_t *keys, int n, const
     return cudaSuccess;
 }
 
-// 4-wide nodes: every binary internal node at even depth becomes one node;
-// its children are its own children where those are leaves, else its
-// grandchildren.  Node index = rank among the even-depth internal nodes in
-// binary order, so the root (binary node 0, depth 0) is node 0.
-__global__ void even_depth_kernel(int n, const int *parent_int, uint32_t *even)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    int d = 0, node = i;
-    while (parent_int[node] >= 0 && d <= 4 * kStackMax) {
-        node = parent_int[node];
-        d++;
-    }
-    even[i] = (d & 1) == 0 ? 1u : 0u;
-}
-
-__device__ __forceinline__ void put_child(float lo[3][4], float hi[3][4], int *ref, int *cnt, int m, int r, int c,
-                                          const float *box)
-{
-    for (int a = 0; a < 3; a++) {
-        lo[a][m] = box[a];
-        hi[a][m] = box[3 + a];
-    }
-    ref[m] = r;
-    cnt[m] = c;
-}
-
-__device__ __forceinline__ void write_node4(float lo[3][4], float hi[3][4], int *ref, int *cnt, int m, float4 *o);
-
-__global__ void pack4_kernel(int n, const int *child, const float *leafbox, const float *nodebox,
-                             const uint32_t *even, const uint32_t *idx4, float4 *nodes)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1 || !even[i]) return;
-    float lo[3][4], hi[3][4];
-    int ref[4], cnt[4], m = 0;
-    for (int j = 0; j < 2; j++) {
-        int c = child[2 * i + j];
-        if (c < 0) {
-            put_child(lo, hi, ref, cnt, m++, c, 1, leafbox + 6 * (int64_t)(~c));
-            continue;
-        }
-        for (int q = 0; q < 2; q++) {
-            int g = child[2 * c + q];
-            if (g < 0) put_child(lo, hi, ref, cnt, m++, g, 1, leafbox + 6 * (int64_t)(~g));
-            else put_child(lo, hi, ref, cnt, m++, (int)idx4[g], 0, nodebox + 6 * (int64_t)g);
-        }
-    }
-    write_node4(lo, hi, ref, cnt, m, nodes + 8 * (int64_t)idx4[i]);
-}
-
-// pads the m filled slots with empty ones and stores the 128-byte node
-__device__ __forceinline__ void write_node4(float lo[3][4], float hi[3][4], int *ref, int *cnt, int m, float4 *o)
-{
-    // empty slots: a point box at (3e38, -3e38, 3e38), which no segment or ray
-    // of a scene reaches
-    const float farbox[6] = {3.0e38f, -3.0e38f, 3.0e38f, 3.0e38f, -3.0e38f, 3.0e38f};
-    // slots in order of box surface, largest first (the packet shadow walk
-    // visits internal children in slot order)
-    for (int i = 1; i < m; i++)
-        for (int j = i; j > 0; j--) {
-            float aj = 0.0f, ap = 0.0f;
-            {
-                const float dx = hi[0][j] - lo[0][j], dy = hi[1][j] - lo[1][j], dz = hi[2][j] - lo[2][j];
-                aj = dx * dy + dy * dz + dz * dx;
-            }
-            {
-                const float dx = hi[0][j - 1] - lo[0][j - 1], dy = hi[1][j - 1] - lo[1][j - 1],
-                            dz = hi[2][j - 1] - lo[2][j - 1];
-                ap = dx * dy + dy * dz + dz * dx;
-            }
-            if (!(aj > ap)) break;
-            for (int a = 0; a < 3; a++) {
-                float t = lo[a][j]; lo[a][j] = lo[a][j - 1]; lo[a][j - 1] = t;
-                t = hi[a][j]; hi[a][j] = hi[a][j - 1]; hi[a][j - 1] = t;
-            }
-            int t = ref[j]; ref[j] = ref[j - 1]; ref[j - 1] = t;
-            t = cnt[j]; cnt[j] = cnt[j - 1]; cnt[j - 1] = t;
-        }
-    while (m < 4) put_child(lo, hi, ref, cnt, m++, kEmptyRef, 0, farbox);
-    unsigned leafmask = 0, packed = 0;
-    for (int k = 0; k < 4; k++) {
-        if (ref[k] < 0 && ref[k] != kEmptyRef) leafmask |= 1u << k;
-        packed |= (unsigned)(cnt[k] & 255) << (8 * k);
-    }
-    o[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
-    o[1] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
-    o[2] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
-    o[3] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
-    o[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
-    o[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
-    o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
-    o[7] = make_float4(__uint_as_float(leafmask), __uint_as_float(packed), 0.0f, 0.0f);
-}
-
-// 4-wide nodes by surface area, top down one level per launch: a node starts
-// from the two children of its binary node and, while it has fewer than four
-// slots, opens the internal slot with the largest box surface into that
-// node's two children.  Internal slots left become the next level's nodes,
-// numbered in allocation order (root 0, then breadth first), so the result
-// does not depend on that order: only the slot contents and their order,
-// fixed by the rule, steer a traversal.
+// ==========================================================================
+// 4-wide nodes, built top down one level per launch.  A node starts from the
+// two children of its binary node; while it has fewer than four slots it
+// opens an internal slot into that node's two children: the one with the
+// largest box surface (surface rule) or, in the even rule, each of the two
+// starting slots once (every binary node at even depth becomes a node).  The
+// slots are then put in order of box surface, largest first: the packet
+// shadow walk visits internal children in slot order.  A node's internal
+// children get consecutive node indices from `ibase` and its leaf children
+// consecutive triangle slots from `lbase` (both in slot order), so a child is
+// found from its base and its rank among the node's children of its kind;
+// the triangles are moved into those slots at the end.  Node indices are
+// handed out in allocation order (root 0, then breadth first); the result
+// does not depend on that order, only on the slot contents and their order.
+// ==========================================================================
 constexpr int kCollapseLevels = (kStackMax - 1) / 3; // each level pushes <= 3 stack entries
 
 __device__ __forceinline__ float box_area(const float *b)
@@ -716,84 +629,154 @@ __device__ __forceinline__ float box_area(const float *b)
 __global__ void collapse_init_kernel(int2 *queue, int *count, int *next)
 {
     queue[0] = make_int2(0, 0);
-    count[0] = 1;
-    for (int l = 1; l <= kCollapseLevels; l++) count[l] = 0;
-    *next = 1;
+    count[0] = 1; // nodes of the current level (count[1]: of the next)
+    count[1] = 0;
+    next[0] = 1;  // internal nodes handed out
+    next[1] = 0;  // triangle slots handed out
 }
 
+template <bool EVEN>
 __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, int *count, int *next,
-                                      const int *child, const float *leafbox, const float *nodebox, float4 *nodes)
+                                      const int *child, const float *leafbox, const float *nodebox, float4 *nodes,
+                                      int *leaf_src)
 {
-    const int n_in = count[level];
+    const int n_in = count[level & 1];
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_in; q += gridDim.x * blockDim.x) {
         const int2 w = qin[q];
         int slot[4] = {child[2 * w.x], child[2 * w.x + 1], 0, 0};
         int m = 2;
-        while (m < 4) {
-            int pick = -1;
-            float best = -1.0f;
-            for (int k = 0; k < m; k++)
+        if (EVEN) {
+            for (int k = 0; k < 2; k++)
                 if (slot[k] >= 0) {
-                    const float a = box_area(nodebox + 6 * (int64_t)slot[k]);
-                    if (pick < 0 || a > best) {
-                        pick = k;
-                        best = a;
-                    }
+                    const int c = slot[k];
+                    slot[k] = child[2 * c];
+                    slot[m++] = child[2 * c + 1];
                 }
-            if (pick < 0) break;
-            const int c = slot[pick];
-            slot[pick] = child[2 * c];
-            slot[m++] = child[2 * c + 1];
-        }
-        int n_int = 0;
-        for (int k = 0; k < m; k++) n_int += slot[k] >= 0;
-        const int base = n_int ? atomicAdd(next, n_int) : 0;
-        const int pos = n_int ? atomicAdd(&count[level + 1], n_int) : 0;
-        float lo[3][4], hi[3][4];
-        int ref[4], cnt[4], j = 0;
-        for (int k = 0; k < m; k++) {
-            const int c = slot[k];
-            if (c < 0) {
-                put_child(lo, hi, ref, cnt, k, c, 1, leafbox + 6 * (int64_t)(~c));
-            } else {
-                put_child(lo, hi, ref, cnt, k, base + j, 0, nodebox + 6 * (int64_t)c);
-                qout[pos + j] = make_int2(c, base + j);
-                j++;
+        } else {
+            while (m < 4) {
+                int pick = -1;
+                float best = -1.0f;
+                for (int k = 0; k < m; k++)
+                    if (slot[k] >= 0) {
+                        const float a = box_area(nodebox + 6 * (int64_t)slot[k]);
+                        if (pick < 0 || a > best) {
+                            pick = k;
+                            best = a;
+                        }
+                    }
+                if (pick < 0) break;
+                const int c = slot[pick];
+                slot[pick] = child[2 * c];
+                slot[m++] = child[2 * c + 1];
             }
         }
-        write_node4(lo, hi, ref, cnt, m, nodes + 8 * (int64_t)w.y);
+        // slot order: box surface, largest first (stable)
+        float area[4];
+        for (int k = 0; k < m; k++)
+            area[k] = box_area(slot[k] < 0 ? leafbox + 6 * (int64_t)(~slot[k]) : nodebox + 6 * (int64_t)slot[k]);
+        for (int i = 1; i < m; i++)
+            for (int j = i; j > 0 && area[j] > area[j - 1]; j--) {
+                float ta = area[j]; area[j] = area[j - 1]; area[j - 1] = ta;
+                int ts = slot[j]; slot[j] = slot[j - 1]; slot[j - 1] = ts;
+            }
+        int n_int = 0, n_leaf = 0;
+        for (int k = 0; k < m; k++) {
+            n_int += slot[k] >= 0;
+            n_leaf += slot[k] < 0;
+        }
+        const int ibase = n_int ? atomicAdd(&next[0], n_int) : 0;
+        const int lbase = n_leaf ? atomicAdd(&next[1], n_leaf) : 0;
+        const int pos = n_int ? atomicAdd(&count[(level + 1) & 1], n_int) : 0;
+        // empty slots: a point box at (3e38, -3e38, 3e38), which no segment or
+        // ray of a scene reaches
+        float lo[3][4], hi[3][4];
+        unsigned leafmask = 0, intmask = 0;
+        int ji = 0, jl = 0;
+        for (int k = 0; k < 4; k++) {
+            const float *b = nullptr;
+            if (k < m && slot[k] < 0) {
+                b = leafbox + 6 * (int64_t)(~slot[k]);
+                leaf_src[lbase + jl++] = ~slot[k];
+                leafmask |= 1u << k;
+            } else if (k < m) {
+                b = nodebox + 6 * (int64_t)slot[k];
+                qout[pos + ji] = make_int2(slot[k], ibase + ji);
+                ji++;
+                intmask |= 1u << k;
+            }
+            for (int a = 0; a < 3; a++) {
+                lo[a][k] = b ? b[a] : (a == 1 ? -3.0e38f : 3.0e38f);
+                hi[a][k] = b ? b[3 + a] : (a == 1 ? -3.0e38f : 3.0e38f);
+            }
+        }
+        float4 *o = nodes + 8 * (int64_t)w.y;
+        o[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+        o[1] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+        o[2] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+        o[3] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+        o[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+        o[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+        o[6] = make_float4(__int_as_float(ibase), __int_as_float(lbase), __uint_as_float(leafmask | (intmask << 4)),
+                           0.0f);
+        o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
 
-// Runs the levels; *done stays false if internal nodes are left after
-// kCollapseLevels levels (a tree too deep for the traversal stack), and the
-// caller then packs by even depth, whose stack use the depth check bounds.
-static cudaError_t collapse_sah(const Exec &ex, int T, const int *child, const float *leafbox, const float *nodebox,
-                                float4 *nodes, bool *done)
+// triangles into the slots the nodes gave their leaves
+__global__ void place_tris_kernel(int T, const int *leaf_src, const float4 *tri_in, float4 *tri_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    const int k = leaf_src[i];
+    for (int c = 0; c < 3; c++) tri_out[3 * (int64_t)i + c] = tri_in[3 * (int64_t)k + c];
+}
+
+// Runs the levels with the given rule.  The surface rule stops after
+// kCollapseLevels levels and leaves *done false if internal nodes are left (a
+// tree too deep for the traversal stack); the even rule runs until every
+// node is written (at most kCollapseLevels levels when the binary depth is
+// within kDepthMax, which the build checks).
+static cudaError_t collapse4(const Exec &ex, int T, bool even, const int *child, const float *leafbox,
+                             const float *nodebox, float4 *nodes, int *leaf_src, bool *done)
 {
     *done = false;
     Tmp qa, qb, cnt, next;
     VPL_TRY(qa.alloc(ex, sizeof(int2) * T));
     VPL_TRY(qb.alloc(ex, sizeof(int2) * T));
-    VPL_TRY(cnt.alloc(ex, sizeof(int) * (kCollapseLevels + 1)));
-    VPL_TRY(next.alloc(ex, sizeof(int)));
+    VPL_TRY(cnt.alloc(ex, sizeof(int) * 2));
+    VPL_TRY(next.alloc(ex, sizeof(int) * 2));
     collapse_init_kernel<<<1, 1, 0, ex.stream>>>(qa.as<int2>(), cnt.as<int>(), next.as<int>());
     VPL_LAUNCHED(ex);
     const unsigned grid = grid_for(T, 256) < 1216u ? grid_for(T, 256) : 1216u;
-    for (int l = 0; l < kCollapseLevels; l++) {
+    for (int l = 0;; l++) {
         const Tmp &in = (l & 1) ? qb : qa, &out = (l & 1) ? qa : qb;
-        collapse_level_kernel<<<grid, 256, 0, ex.stream>>>(l, in.as<int2>(), out.as<int2>(), cnt.as<int>(),
-                                                           next.as<int>(), child, leafbox, nodebox, nodes);
+        VPL_TRY(cudaMemsetAsync(cnt.as<int>() + ((l + 1) & 1), 0, sizeof(int), ex.stream));
+        if (even)
+            collapse_level_kernel<true><<<grid, 256, 0, ex.stream>>>(l, in.as<int2>(), out.as<int2>(), cnt.as<int>(),
+                                                                     next.as<int>(), child, leafbox, nodebox, nodes,
+                                                                     leaf_src);
+        else
+            collapse_level_kernel<false><<<grid, 256, 0, ex.stream>>>(l, in.as<int2>(), out.as<int2>(),
+                                                                      cnt.as<int>(), next.as<int>(), child, leafbox,
+                                                                      nodebox, nodes, leaf_src);
         VPL_LAUNCHED(ex);
+        const bool last = !even && l + 1 == kCollapseLevels;
+        if (last || (l + 1) % 16 == 0) {
+            int left = 0;
+            VPL_TRY(cudaMemcpyAsync(&left, cnt.as<int>() + ((l + 1) & 1), sizeof(int), cudaMemcpyDeviceToHost,
+                                    ex.stream));
+            VPL_TRY(cudaStreamSynchronize(ex.stream));
+            if (left == 0) {
+                *done = true;
+                break;
+            }
+            if (last) break;
+        }
     }
-    int left = 0;
-    VPL_TRY(cudaMemcpyAsync(&left, cnt.as<int>() + kCollapseLevels, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
-    VPL_TRY(cudaStreamSynchronize(ex.stream));
-    *done = left == 0;
     return cudaSuccess;
 }
 
-// one triangle: a root with the leaf in slot 0 and three empty slots
+// one triangle: a root with the leaf (slot 0) in slot 0 and three empty slots
 __global__ void single_root_kernel(const float *leafbox, float4 *nodes)
 {
     const float *a = leafbox;
@@ -804,9 +787,8 @@ __global__ void single_root_kernel(const float *leafbox, float4 *nodes)
     nodes[3] = make_float4(a[4], -f, -f, -f);
     nodes[4] = make_float4(a[2], f, f, f);
     nodes[5] = make_float4(a[5], f, f, f);
-    nodes[6] = make_float4(__int_as_float(~0), __int_as_float(kEmptyRef), __int_as_float(kEmptyRef),
-                           __int_as_float(kEmptyRef));
-    nodes[7] = make_float4(__uint_as_float(1u), __uint_as_float(1u), 0.0f, 0.0f);
+    nodes[6] = make_float4(__int_as_float(0), __int_as_float(0), __uint_as_float(1u), 0.0f);
+    nodes[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 __global__ void depth_kernel(int n, const int *parent_int, const int *parent_leaf, int *depth, int *status)
@@ -871,14 +853,17 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
     VPL_TRY(radix_sort_pairs(ex, keys.as<uint64_t>(), vals.as<uint32_t>(), nullptr, T));
 
     VPL_TRY(leafbox.alloc(ex, sizeof(float) * 6 * T));
-    leaves_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(sb->verts, sb->idx, vals.as<uint32_t>(), T, sb->vbox, sb->tri,
-                                                       leafbox.as<float>());
+    Tmp trim;
+    VPL_TRY(trim.alloc(ex, sizeof(float4) * 3 * T));
+    leaves_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(sb->verts, sb->idx, vals.as<uint32_t>(), T, sb->vbox,
+                                                       trim.as<float4>(), leafbox.as<float>());
     VPL_LAUNCHED(ex);
     VPL_TRY(pleaf.alloc(ex, sizeof(int) * T));
     VPL_TRY(pint.alloc(ex, sizeof(int) * (T > 1 ? T - 1 : 1)));
     if (T == 1) {
         single_root_kernel<<<1, 1, 0, ex.stream>>>(leafbox.as<float>(), sb->nodes);
         VPL_LAUNCHED(ex);
+        VPL_TRY(cudaMemcpyAsync(sb->tri, trim.p, sizeof(float4) * 3, cudaMemcpyDeviceToDevice, ex.stream));
     } else {
         VPL_TRY(nodebox.alloc(ex, sizeof(float) * 6 * (T - 1)));
         VPL_TRY(child.alloc(ex, sizeof(int) * 2 * (T - 1)));
@@ -890,22 +875,18 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
         if (!built)
             VPL_TRY(lbvh_build(ex, keys.as<uint64_t>(), n, leafbox.as<float>(), child.as<int>(), nodebox.as<float>(),
                                pint.as<int>(), pleaf.as<int>()));
+        Tmp leaf_src;
+        VPL_TRY(leaf_src.alloc(ex, sizeof(int) * T));
         bool packed = false;
 #if !VPL_BVH_EVEN_COLLAPSE
-        VPL_TRY(collapse_sah(ex, n, child.as<int>(), leafbox.as<float>(), nodebox.as<float>(), sb->nodes, &packed));
+        VPL_TRY(collapse4(ex, n, false, child.as<int>(), leafbox.as<float>(), nodebox.as<float>(), sb->nodes,
+                          leaf_src.as<int>(), &packed));
 #endif
-        if (!packed) {
-            Tmp even, idx4;
-            VPL_TRY(even.alloc(ex, sizeof(uint32_t) * (T - 1)));
-            VPL_TRY(idx4.alloc(ex, sizeof(uint32_t) * T));
-            even_depth_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, pint.as<int>(), even.as<uint32_t>());
-            VPL_LAUNCHED(ex);
-            VPL_TRY(exclusive_scan<uint32_t>(ex, even.as<uint32_t>(), idx4.as<uint32_t>(), nullptr, T - 1));
-            pack4_kernel<<<grid_for(T - 1, B), B, 0, ex.stream>>>(n, child.as<int>(), leafbox.as<float>(),
-                                                                  nodebox.as<float>(), even.as<uint32_t>(),
-                                                                  idx4.as<uint32_t>(), sb->nodes);
-            VPL_LAUNCHED(ex);
-        }
+        if (!packed)
+            VPL_TRY(collapse4(ex, n, true, child.as<int>(), leafbox.as<float>(), nodebox.as<float>(), sb->nodes,
+                              leaf_src.as<int>(), &packed));
+        place_tris_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(n, leaf_src.as<int>(), trim.as<float4>(), sb->tri);
+        VPL_LAUNCHED(ex);
     }
     depth_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(n, pint.as<int>(), pleaf.as<int>(), sb->depth, ex.status);
     VPL_LAUNCHED(ex);

@@ -209,30 +209,35 @@ __device__ __forceinline__ bool tri_hit(const Ray &r, float4 v0, float4 e1v, flo
 }
 
 // --------------------------------------------------------------------------
-// 4-wide BVH nodes (8 float4 = 128 B): lo.x / hi.x / lo.y / hi.y / lo.z / hi.z
-// of the four children, their references (>= 0 node, < 0 leaf ~first
-// triangle slot, kEmptyRef none) and the triangle count of leaf children.
+// 4-wide BVH nodes (8 float4 = 128 B): rows 0-5 lo.x / hi.x / lo.y / hi.y /
+// lo.z / hi.z of the four child slots; row 6 (ibase, lbase, masks, 0) with
+// masks bits 0-3 = leaf slots, bits 4-7 = internal slots; row 7 unused.  A
+// node's internal children are nodes ibase, ibase + 1, ... and its leaves
+// (one triangle each) triangle slots lbase, lbase + 1, ..., both in slot
+// order; an empty slot holds a box no segment reaches.
 // --------------------------------------------------------------------------
 constexpr int kEmptyRef = (int)0x80000000;
 
 struct Node4 {
     float4 lx, hx, ly, hy, lz, hz;
-    int ref[4], cnt[4];
-    unsigned leafmask; // bit k set: child k is a leaf
+    int ibase, lbase;           // first internal child node / first leaf triangle slot
+    unsigned leafmask, intmask; // bit k: slot k holds a leaf / an internal node
+    int ref[4], cnt[4];         // decoded per slot (load_node4 only)
 };
 
-// child references, leaf mask and leaf triangle counts (rows 6 and 7)
+// child bases and slot masks (row 6)
 __device__ __forceinline__ void load_node4_meta(const float4 *p, Node4 &n)
 {
-    float4 r = __ldg(p + 6), c = __ldg(p + 7);
-    n.ref[0] = __float_as_int(r.x); n.ref[1] = __float_as_int(r.y);
-    n.ref[2] = __float_as_int(r.z); n.ref[3] = __float_as_int(r.w);
-    n.leafmask = __float_as_uint(c.x);
-    const unsigned packed = __float_as_uint(c.y); // 8-bit triangle counts of leaf children
-    n.cnt[0] = packed & 255u; n.cnt[1] = (packed >> 8) & 255u;
-    n.cnt[2] = (packed >> 16) & 255u; n.cnt[3] = packed >> 24;
+    const float4 r = __ldg(p + 6);
+    n.ibase = __float_as_int(r.x);
+    n.lbase = __float_as_int(r.y);
+    const unsigned m = __float_as_uint(r.z);
+    n.leafmask = m & 15u;
+    n.intmask = (m >> 4) & 15u;
 }
 
+// whole node, with each slot's reference decoded: >= 0 internal node,
+// < 0 leaf (~triangle slot, cnt 1), kEmptyRef none
 __device__ __forceinline__ void load_node4(const float4 *nodes, int node, Node4 &n)
 {
     const float4 *p = nodes + 8 * (int64_t)node;
@@ -242,13 +247,21 @@ __device__ __forceinline__ void load_node4(const float4 *nodes, int node, Node4 
     n.hy = __ldg(p + 3);
     n.lz = __ldg(p + 4);
     n.hz = __ldg(p + 5);
-    float4 r = __ldg(p + 6), c = __ldg(p + 7);
-    n.ref[0] = __float_as_int(r.x); n.ref[1] = __float_as_int(r.y);
-    n.ref[2] = __float_as_int(r.z); n.ref[3] = __float_as_int(r.w);
-    n.leafmask = __float_as_uint(c.x);
-    const unsigned packed = __float_as_uint(c.y); // 8-bit triangle counts of leaf children
-    n.cnt[0] = packed & 255u; n.cnt[1] = (packed >> 8) & 255u;
-    n.cnt[2] = (packed >> 16) & 255u; n.cnt[3] = packed >> 24;
+    load_node4_meta(p, n);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const unsigned below = (1u << k) - 1u;
+        if ((n.leafmask >> k) & 1u) {
+            n.ref[k] = ~(n.lbase + __popc(n.leafmask & below));
+            n.cnt[k] = 1;
+        } else if ((n.intmask >> k) & 1u) {
+            n.ref[k] = n.ibase + __popc(n.intmask & below);
+            n.cnt[k] = 0;
+        } else {
+            n.ref[k] = kEmptyRef;
+            n.cnt[k] = 0;
+        }
+    }
 }
 
 __device__ __forceinline__ float fmin3(float a, float b, float c)
@@ -527,16 +540,13 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
                 if (todo != 0 && !occl) {
                     const int k = __ffs(todo) - 1;
                     todo &= todo - 1;
-                    const int first = ~(k == 0 ? n.ref[0] : k == 1 ? n.ref[1] : k == 2 ? n.ref[2] : n.ref[3]);
-                    const int c = k == 0 ? n.cnt[0] : k == 1 ? n.cnt[1] : k == 2 ? n.cnt[2] : n.cnt[3];
-                    for (int q = first; q < first + c && !occl; q++) {
-                        float t;
-                        if (COUNT) wc.tests++;
-                        if (tri_hit(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2), t) &&
-                            t > 0.0f && t < 1.0f) {
-                            occl = true;
-                            cache = q;
-                        }
+                    const int q = n.lbase + __popc(leafmask & ((1u << k) - 1u));
+                    float t;
+                    if (COUNT) wc.tests++;
+                    if (tri_hit(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2), t) &&
+                        t > 0.0f && t < 1.0f) {
+                        occl = true;
+                        cache = q;
                     }
                 }
             }
@@ -544,7 +554,7 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
             if (alive == 0) break;
             any = __reduce_or_sync(kFull, occl ? 0u : hits);
         }
-        unsigned need = any & ~leafmask;
+        unsigned need = any & n.intmask;
         if (need) {
             const int pick = __ffs(need) - 1;
             need &= need - 1;
@@ -552,10 +562,9 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
             // lanes 0-3 push the other children at once, lowest slot on top
             const int mk = lane & 3;
             if (lane < 4 && ((need >> mk) & 1u))
-                stk[sp + __popc(need >> (mk + 1))] =
-                    mk == 0 ? n.ref[0] : mk == 1 ? n.ref[1] : mk == 2 ? n.ref[2] : n.ref[3];
+                stk[sp + __popc(need >> (mk + 1))] = n.ibase + __popc(n.intmask & ((1u << mk) - 1u));
             sp += __popc(need);
-            node = pick == 0 ? n.ref[0] : pick == 1 ? n.ref[1] : pick == 2 ? n.ref[2] : n.ref[3];
+            node = n.ibase + __popc(n.intmask & ((1u << pick) - 1u));
         } else {
             if (sp == 0) break;
             __syncwarp();
