@@ -205,7 +205,10 @@ VPL_API int vpl_generate(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam
 VPL_API int vpl_generate_info(vpl_ctx *ctx, vpl_gen_info *out);
 
 /* Step (4): out_rgba (device float4[width*height]) receives, per pixel,
- * (rho/pi) * sum_i flux_i cos_i cos_y / (pi max(d^2, d2_min)) * V_i. */
+ * (rho/pi) * sum_i flux_i cos_i cos_y / (pi max(d^2, d2_min)) * V_i.
+ * The sum runs over the VPLs in the Morton order of their positions (a
+ * stable sort made on the stream for each call; it only changes FP32
+ * rounding, and makes neighbouring shadow rays of a warp share BVH work). */
 VPL_API int vpl_gather(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf,
                const vpl_vpl_set *vpls, const vpl_gather_params *params, float *out_rgba,
                vpl_stream stream);
@@ -217,7 +220,9 @@ VPL_API int vpl_gather(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf
  * application, or code where an allocation could block on or synchronise
  * with other work on the device.  Arguments, results and errors are those of
  * vpl_gather; the caller passes every input and output buffer, and this call
- * makes no cudaMalloc/cudaFree, pool or other allocating call.
+ * makes no cudaMalloc/cudaFree, pool or other allocating call.  It sums the
+ * VPLs in the order given (sorting them would need scratch), so its image
+ * equals vpl_gather's up to FP32 rounding, not bit for bit, and it is slower.
  * Its one piece of scratch, the tile counter of the gather's dynamic
  * scheduler, sits in a 256-byte static device array of the library that
  * every GPU which loads libvpl holds until the process exits.  The first

@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint6
     }
 }
 
-cudaError_t radix_sort_pairs(const Exec &ex, uint64_t *keys, uint32_t *vals, const int *n_dev, int64_t n_max)
+cudaError_t radix_sort_pairs(const Exec &ex, uint64_t *keys, uint32_t *vals, const int *n_dev, int64_t n_max,
+                             int key_bits)
 {
     if (n_max <= 0) return cudaSuccess;
     const int n_tiles = (int)((n_max + kSortTile - 1) / kSortTile);
@@ -195,7 +196,8 @@ cudaError_t radix_sort_pairs(const Exec &ex, uint64_t *keys, uint32_t *vals, con
     VPL_TRY(off.alloc(ex, sizeof(uint32_t) * (256 * (int64_t)n_tiles + 1)));
     uint64_t *ka = keys, *kb = k2.as<uint64_t>();
     uint32_t *va = vals, *vb = v2.as<uint32_t>();
-    for (int shift = 0; shift < 64; shift += 8) {
+    const int passes = ((key_bits + 15) / 16) * 2; // even: the result ends where it started
+    for (int shift = 0; shift < 8 * passes && shift < 64; shift += 8) {
         radix_hist_kernel<<<n_tiles, kSortThreads, 0, ex.stream>>>(ka, n_dev, n_max, shift, hist.as<uint32_t>(), n_tiles);
         VPL_LAUNCHED(ex);
         VPL_TRY(exclusive_scan<uint32_t>(ex, hist.as<uint32_t>(), off.as<uint32_t>(), nullptr, 256 * (int64_t)n_tiles));
@@ -205,7 +207,7 @@ cudaError_t radix_sort_pairs(const Exec &ex, uint64_t *keys, uint32_t *vals, con
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
-    // eight passes: the result is back in keys / vals
+    // an even number of passes: the result is back in keys / vals
     return cudaSuccess;
 }
 
@@ -259,31 +261,63 @@ __global__ void validate_kernel(int32_t *tris, int64_t n_tris, int64_t n_verts, 
     }
 }
 
+__device__ __forceinline__ unsigned long long warp_min64(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// per-triangle normal and albedo; the centroid and vertex boxes are reduced
+// over each warp first, so each warp makes one atomic per bound
 __global__ void prep_kernel(const float *verts, const int32_t *tris, const float *albedo, int64_t n_tris,
                             int64_t n_verts, float4 *nrm, float4 *rho, BoxKeys *bk)
 {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tris) return;
-    int32_t i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
-    if (i0 < 0 || i0 >= n_verts || i1 < 0 || i1 >= n_verts || i2 < 0 || i2 >= n_verts) {
-        nrm[t] = make_float4(0, 0, 0, 0);
-        rho[t] = make_float4(0, 0, 0, 0);
-        return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long glo[3] = {~0ULL, ~0ULL, ~0ULL}, ghi[3] = {0ULL, 0ULL, 0ULL};
+    unsigned vlo[3] = {~0u, ~0u, ~0u}, vhi[3] = {0u, 0u, 0u};
+    if (t < n_tris) {
+        const int32_t i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+        if (i0 < 0 || i0 >= n_verts || i1 < 0 || i1 >= n_verts || i2 < 0 || i2 >= n_verts) {
+            nrm[t] = make_float4(0, 0, 0, 0);
+            rho[t] = make_float4(0, 0, 0, 0);
+        } else {
+            D3 a = dvert(verts, i0), b = dvert(verts, i1), c = dvert(verts, i2);
+            D3 cr = dcross(dsub(b, a), dsub(c, a));
+            double l = __dsqrt_rn(ddot(cr, cr));
+            D3 n = l > 0.0 ? dmk(__ddiv_rn(cr.x, l), __ddiv_rn(cr.y, l), __ddiv_rn(cr.z, l)) : dmk(0, 0, 0);
+            nrm[t] = make_float4((float)n.x, (float)n.y, (float)n.z, 0.0f);
+            rho[t] = make_float4(albedo[3 * t], albedo[3 * t + 1], albedo[3 * t + 2], 0.0f);
+            D3 s = dadd(dadd(a, b), c);
+            const double g[3] = {__ddiv_rn(s.x, 3.0), __ddiv_rn(s.y, 3.0), __ddiv_rn(s.z, 3.0)};
+            for (int ax = 0; ax < 3; ax++) {
+                glo[ax] = ghi[ax] = dkey(g[ax]);
+                const float v0 = verts[3 * (int64_t)i0 + ax], v1 = verts[3 * (int64_t)i1 + ax],
+                            v2 = verts[3 * (int64_t)i2 + ax];
+                vlo[ax] = fkey(fminf(v0, fminf(v1, v2)));
+                vhi[ax] = fkey(fmaxf(v0, fmaxf(v1, v2)));
+            }
+        }
     }
-    D3 a = dvert(verts, i0), b = dvert(verts, i1), c = dvert(verts, i2);
-    D3 cr = dcross(dsub(b, a), dsub(c, a));
-    double l = __dsqrt_rn(ddot(cr, cr));
-    D3 n = l > 0.0 ? dmk(__ddiv_rn(cr.x, l), __ddiv_rn(cr.y, l), __ddiv_rn(cr.z, l)) : dmk(0, 0, 0);
-    nrm[t] = make_float4((float)n.x, (float)n.y, (float)n.z, 0.0f);
-    rho[t] = make_float4(albedo[3 * t], albedo[3 * t + 1], albedo[3 * t + 2], 0.0f);
-    D3 s = dadd(dadd(a, b), c);
-    double g[3] = {__ddiv_rn(s.x, 3.0), __ddiv_rn(s.y, 3.0), __ddiv_rn(s.z, 3.0)};
     for (int ax = 0; ax < 3; ax++) {
-        atomicMin(&bk->glo[ax], dkey(g[ax]));
-        atomicMax(&bk->ghi[ax], dkey(g[ax]));
-        float v0 = verts[3 * (int64_t)i0 + ax], v1 = verts[3 * (int64_t)i1 + ax], v2 = verts[3 * (int64_t)i2 + ax];
-        atomicMin(&bk->vlo[ax], fkey(fminf(v0, fminf(v1, v2))));
-        atomicMax(&bk->vhi[ax], fkey(fmaxf(v0, fmaxf(v1, v2))));
+        const unsigned long long lo = warp_min64(glo[ax]), hi = warp_max64(ghi[ax]);
+        const unsigned flo = __reduce_min_sync(kFull, vlo[ax]), fhi = __reduce_max_sync(kFull, vhi[ax]);
+        if ((threadIdx.x & 31) == 0 && hi >= lo) { // some lane of the warp had a valid triangle
+            atomicMin(&bk->glo[ax], lo);
+            atomicMax(&bk->ghi[ax], hi);
+            atomicMin(&bk->vlo[ax], flo);
+            atomicMax(&bk->vhi[ax], fhi);
+        }
     }
 }
 

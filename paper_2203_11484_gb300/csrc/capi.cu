@@ -47,6 +47,7 @@ struct vpl_ctx {
         ViewDesc *views = nullptr; // device table, sorted by first tile
         int *counter = nullptr;    // the launch's tile counter
         int n_views = 0, n_tiles = 0, tile_shift = 3;
+        int64_t n_vpls = 0;        // VPLs of all views
     };
     std::map<uint64_t, Batch> batches;
     uint64_t next_batch = 1;
@@ -544,7 +545,8 @@ namespace {
 // host view table of a batch: views with the most VPLs first, tile ranges
 // in that order
 int build_view_table(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, const vpl_vpl_set *vpls,
-                     float *const *out_rgba, int32_t tile_w, std::vector<ViewDesc> &h, int64_t &tiles)
+                     float *const *out_rgba, int32_t tile_w, std::vector<ViewDesc> &h, int64_t &tiles,
+                     int64_t &n_vpls)
 {
     if (n_views < 1 || !gbufs || !vpls || !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "bad batch arrays");
     if (tile_w != 0 && tile_w != 4 && tile_w != 8 && tile_w != 16 && tile_w != 32)
@@ -566,6 +568,7 @@ int build_view_table(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, co
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return vpls[a].count > vpls[b].count; });
     h.assign(n_views, ViewDesc());
     tiles = 0;
+    n_vpls = 0;
     for (int k = 0; k < n_views; k++) {
         const int i = order[k];
         ViewDesc &d = h[k];
@@ -575,6 +578,9 @@ int build_view_table(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, co
         d.count = vpls[i].count;
         d.tiles_x = (int32_t)((gbufs[i].width + tw - 1) / tw);
         d.tile_begin = (int32_t)tiles;
+        d.vpl_begin = (int32_t)n_vpls;
+        n_vpls += vpls[i].count;
+        if (n_vpls > INT32_MAX) return fail(ctx, VPL_ERR_INVALID_ARG, "batch has more than 2^31 - 1 VPLs");
         d.g_pos = (const float4 *)gbufs[i].pos;
         d.g_nrm = gbufs[i].nrm;
         d.g_alb = gbufs[i].albedo;
@@ -603,7 +609,8 @@ int vpl_gather_views(vpl_ctx *ctx, vpl_scene_id scene, int32_t n_views, const vp
     if (rc) return rc;
     std::vector<ViewDesc> h;
     int64_t tiles = 0;
-    if ((rc = build_view_table(ctx, n_views, gbufs, vpls, out_rgba, params->tile_w, h, tiles))) return rc;
+    int64_t n_vpls = 0;
+    if ((rc = build_view_table(ctx, n_views, gbufs, vpls, out_rgba, params->tile_w, h, tiles, n_vpls))) return rc;
     if (gbufs[0].format != fmt) return fail(ctx, VPL_ERR_INVALID_ARG, "buffer format does not match the precision");
     DeviceGuard g(ctx->device);
     Exec ex = exec_of(ctx, stream);
@@ -620,7 +627,7 @@ int vpl_gather_views(vpl_ctx *ctx, vpl_scene_id scene, int32_t n_views, const vp
     a.visibility = params->visibility;
     a.blocks_per_sm = params->blocks_per_sm;
     CK(ctx, gather_batch(ex, view_of(s), a, table.as<ViewDesc>(), n_views, (int)tiles,
-                         tile_shift_of(params->tile_w), counter.as<int>()),
+                         tile_shift_of(params->tile_w), counter.as<int>(), n_vpls),
        "vpl_gather_views");
     return VPL_OK;
 }
@@ -633,11 +640,13 @@ int vpl_batch_create(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, co
     *out = 0;
     std::vector<ViewDesc> h;
     int64_t tiles = 0;
-    int rc = build_view_table(ctx, n_views, gbufs, vpls, out_rgba, tile_w, h, tiles);
+    int64_t n_vpls = 0;
+    int rc = build_view_table(ctx, n_views, gbufs, vpls, out_rgba, tile_w, h, tiles, n_vpls);
     if (rc) return rc;
     DeviceGuard g(ctx->device);
     vpl_ctx::Batch b;
     b.n_views = n_views;
+    b.n_vpls = n_vpls;
     b.n_tiles = (int)tiles;
     b.tile_shift = tile_shift_of(tile_w);
     CK(ctx, cudaMalloc(&b.views, sizeof(ViewDesc) * n_views), "vpl_batch_create");
@@ -686,7 +695,8 @@ int vpl_gather_batch(vpl_ctx *ctx, vpl_scene_id scene, vpl_batch_id batch, const
     a.visibility = params->visibility;
     a.blocks_per_sm = params->blocks_per_sm;
     const vpl_ctx::Batch &b = it->second;
-    CK(ctx, gather_batch(exec_of(ctx, stream), view_of(s), a, b.views, b.n_views, b.n_tiles, b.tile_shift, b.counter),
+    CK(ctx, gather_batch(exec_of(ctx, stream), view_of(s), a, b.views, b.n_views, b.n_tiles, b.tile_shift, b.counter,
+                         b.n_vpls),
        "vpl_gather_batch");
     return VPL_OK;
 }

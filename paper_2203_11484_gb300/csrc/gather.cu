@@ -99,6 +99,7 @@ struct GatherExtra {
     const int32_t *dbg_pixels;        // DEBUG: pixel list, else null
     int64_t n_dbg;
     int8_t *dbg_vis;
+    const uint32_t *v_order;          // VPLs in this order (per view from vpl_begin), else as given
 };
 
 template <int VIS, int PREC, bool COUNT, bool DEBUG, bool BATCH>
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
         const float4 *g_pos = a.g_pos, *v_pos = a.v_pos;
         const void *g_nrm = a.g_nrm, *g_alb = a.g_alb, *v_nrm = a.v_nrm, *v_flux = a.v_flux;
         float4 *out = a.out;
+        int vbeg = 0;
         if (BATCH) {
             int lo = 0, hi = e.n_views;
             while (hi - lo > 1) {
@@ -140,7 +142,9 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
             v_nrm = vd->v_nrm;
             v_flux = vd->v_flux;
             out = vd->out;
+            vbeg = vd->vpl_begin;
         }
+        const uint32_t *ord = e.v_order ? e.v_order + vbeg : nullptr;
         int64_t p;
         bool inb; // pixel exists (in the image / in the debug list)
         if (DEBUG) {
@@ -169,15 +173,16 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
             if (__shfl_sync(kFull, st, 0) == VPL_ERR_TRAVERSAL_LIMIT) break;
             const int i = base + lane;
             if (i < M) {
-                const float4 vp = __ldg(v_pos + i);
-                float4 vf = load_attr(v_flux, i, gfmt);
+                const int src = ord ? (int)__ldg(ord + i) : i;
+                const float4 vp = __ldg(v_pos + src);
+                float4 vf = load_attr(v_flux, src, gfmt);
                 if (gfmt == VPL_FORMAT_FP16) { // FP16 colour x FP32 magnitude (pos.w)
                     vf.x *= vp.w;
                     vf.y *= vp.w;
                     vf.z *= vp.w;
                 }
                 stage[wid][0][lane] = vp;
-                stage[wid][1][lane] = load_attr(v_nrm, i, gfmt);
+                stage[wid][1][lane] = load_attr(v_nrm, src, gfmt);
                 stage[wid][2][lane] = vf;
             }
             __syncwarp();
@@ -202,7 +207,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                     n_rays += want ? 1 : 0;
                     n_blocked += (want && !vis) ? 1 : 0;
                 }
-                if (DEBUG && inb) e.dbg_vis[((int64_t)tile * 32 + lane) * M + base + j] = want ? (vis ? 1 : 0) : -1;
+                if (DEBUG && inb) {
+                    const int64_t v = ord ? (int64_t)__ldg(ord + base + j) : base + j; // as given
+                    e.dbg_vis[((int64_t)tile * 32 + lane) * M + v] = want ? (vis ? 1 : 0) : -1;
+                }
                 if (want && vis) {
                     const float g = __fdividef(cosi * cosy, d2 * fmaxf(d2, d2min));
                     if (PREC == VPL_PREC_FP16_KAHAN) {
@@ -299,7 +307,60 @@ static GatherExtra single_view_extra(const GatherArgs &a, int *counter)
     e.dbg_pixels = nullptr;
     e.n_dbg = 0;
     e.dbg_vis = nullptr;
+    e.v_order = nullptr;
     return e;
+}
+
+// ---------------------------------------------------------------------------
+// VPL order of a gather.  The image is the same sum in any order (up to FP32
+// rounding); the order only steers speed: consecutive VPLs close in space
+// send each warp's shadow packets through the same part of the BVH and let
+// the per-pixel occluder cache hit.  Order = 30-bit Morton code of the VPL
+// position in the scene box, ties by index (a stable sort); in a batch each
+// view's VPLs are ordered on their own (view index above the code).
+// ---------------------------------------------------------------------------
+__global__ void vpl_order_keys_kernel(const double *gbox, const float4 *v_pos, const ViewDesc *views, int n_views,
+                                      int64_t total, uint64_t *keys, uint32_t *vals)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int view = 0;
+    int64_t local = g;
+    const float4 *vp = v_pos;
+    if (views) {
+        int lo = 0, hi = n_views;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (views[mid].vpl_begin <= g) lo = mid; else hi = mid;
+        }
+        view = lo;
+        local = g - views[lo].vpl_begin;
+        vp = views[lo].v_pos;
+    }
+    const float4 p = __ldg(vp + local);
+    const float c[3] = {p.x, p.y, p.z};
+    uint32_t q[3];
+    for (int a = 0; a < 3; a++) {
+        const float lo = (float)gbox[a], ext = (float)gbox[3 + a] - lo;
+        const float u = ext > 0.0f ? (c[a] - lo) / ext : 0.0f;
+        q[a] = (uint32_t)fminf(fmaxf(floorf(u * 1024.0f), 0.0f), 1023.0f);
+    }
+    keys[g] = ((uint64_t)view << 32) | morton63(q[0], q[1], q[2]);
+    vals[g] = (uint32_t)local;
+}
+
+static cudaError_t vpl_order(const Exec &ex, const SceneView &s, const float4 *v_pos, const ViewDesc *views,
+                             int n_views, int64_t total, Tmp &order)
+{
+    Tmp keys;
+    VPL_TRY(keys.alloc(ex, sizeof(uint64_t) * total));
+    VPL_TRY(order.alloc(ex, sizeof(uint32_t) * total));
+    vpl_order_keys_kernel<<<grid_for(total, 256), 256, 0, ex.stream>>>(s.gbox, v_pos, views, n_views, total,
+                                                                       keys.as<uint64_t>(), order.as<uint32_t>());
+    VPL_LAUNCHED(ex);
+    int bits = 32;
+    while (bits < 64 && ((int64_t)1 << (bits - 32)) < n_views) bits++;
+    return radix_sort_pairs(ex, keys.as<uint64_t>(), order.as<uint32_t>(), nullptr, total, bits);
 }
 
 static cudaError_t run_gather(const Exec &ex, const SceneView &s, const GatherArgs &a, bool count,
@@ -308,10 +369,14 @@ static cudaError_t run_gather(const Exec &ex, const SceneView &s, const GatherAr
     const int64_t npx = (int64_t)a.width * a.height;
     if (pixels == nullptr && npx == 0) return cudaSuccess;
     if (pixels != nullptr && n_pixels == 0) return cudaSuccess;
-    Tmp ctr;
+    Tmp ctr, order;
     VPL_TRY(ctr.alloc(ex, sizeof(int)));
     VPL_TRY(cudaMemsetAsync(ctr.p, 0, sizeof(int), ex.stream));
     GatherExtra e = single_view_extra(a, ctr.as<int>());
+    if (a.count > 1) {
+        VPL_TRY(vpl_order(ex, s, a.v_pos, nullptr, 1, a.count, order));
+        e.v_order = order.as<uint32_t>();
+    }
     if (pixels) e.n_tiles = (int)((n_pixels + 31) / 32);
     e.counters = counters;
     e.dbg_pixels = pixels;
@@ -324,11 +389,16 @@ static cudaError_t run_gather(const Exec &ex, const SceneView &s, const GatherAr
 
 // many views in one persistent launch: tiles of all views in one queue
 cudaError_t gather_batch(const Exec &ex, const SceneView &s, const GatherArgs &a, const ViewDesc *views, int n_views,
-                         int n_tiles, int tile_shift, int *counter)
+                         int n_tiles, int tile_shift, int *counter, int64_t n_vpls)
 {
     if (n_tiles == 0) return cudaSuccess;
     VPL_TRY(cudaMemsetAsync(counter, 0, sizeof(int), ex.stream));
     GatherExtra e = single_view_extra(a, counter);
+    Tmp order;
+    if (n_vpls > 1) {
+        VPL_TRY(vpl_order(ex, s, nullptr, views, n_views, n_vpls, order));
+        e.v_order = order.as<uint32_t>();
+    }
     e.views = views;
     e.n_views = n_views;
     e.n_tiles = n_tiles;

@@ -57,10 +57,11 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 template <typename T>
 cudaError_t exclusive_scan(const Exec &ex, const T *in, T *out, const int *n_dev, int64_t n_max);
 
-// stable LSD radix sort of (key, value) pairs on bits [0, 64); the result
-// ends in keys/vals.  Count from n_dev when given.
+// stable LSD radix sort of (key, value) pairs on bits [0, key_bits) (keys
+// must be zero above); the result ends in keys/vals.  Count from n_dev when
+// given.
 cudaError_t radix_sort_pairs(const Exec &ex, uint64_t *keys, uint32_t *vals, const int *n_dev,
-                             int64_t n_max);
+                             int64_t n_max, int key_bits = 64);
 
 struct SceneBuffers {
     int64_t n_tris = 0, n_verts = 0;
@@ -124,7 +125,7 @@ struct GatherArgs {
 // views in order of their first tile)
 struct ViewDesc {
     int32_t width, height, count, tiles_x;
-    int32_t tile_begin, pad0, pad1, pad2;
+    int32_t tile_begin, vpl_begin, pad1, pad2; // first tile / first entry in the batch's VPL order array
     const float4 *g_pos;
     const void *g_nrm, *g_alb;
     const float4 *v_pos;
@@ -135,7 +136,7 @@ struct ViewDesc {
 
 int tile_shift_of(int tile_w);
 cudaError_t gather_batch(const Exec &ex, const SceneView &s, const GatherArgs &a, const ViewDesc *views, int n_views,
-                         int n_tiles, int tile_shift, int *counter);
+                         int n_tiles, int tile_shift, int *counter, int64_t n_vpls);
 
 cudaError_t gbuffer_build(const Exec &ex, const SceneView &s, const CamArgs &c, bool brute,
                           float4 *pos, void *nrm, void *alb, int format);
