@@ -242,10 +242,12 @@ VPL_API int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuff
  * with the most VPLs first.  vpl_batch_create copies a device table of the
  * views (synchronously; the buffers must stay allocated while the batch is
  * used) and fixes the tile width (tile_w as in vpl_gather_params, 0 = 8);
- * vpl_gather_batch then enqueues only a memset and one kernel, so it can be
- * captured in a CUDA graph.  Each pixel's sum runs in VPL order within one
- * thread: images equal those of vpl_gather per view.  Calls with the same
- * batch must not overlap on the GPU (they share its tile counter). */
+ * vpl_gather_batch then enqueues the VPL sort of all views (pool memory on
+ * the stream), a memset and one gather kernel; it can be captured in a CUDA
+ * graph.  Each pixel's sum runs in the view's VPL order (as in vpl_gather)
+ * within one thread: images equal those of vpl_gather per view.  Calls with
+ * the same batch must not overlap on the GPU (they share its tile counter).
+ * At most 2^22 views and 2^31 - 1 VPLs in all. */
 typedef uint64_t vpl_batch_id;
 VPL_API int vpl_batch_create(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs,
                              const vpl_vpl_set *vpls, float *const *out_rgba, int32_t tile_w,

@@ -549,6 +549,7 @@ int build_view_table(vpl_ctx *ctx, int32_t n_views, const vpl_gbuffer *gbufs, co
                      int64_t &n_vpls)
 {
     if (n_views < 1 || !gbufs || !vpls || !out_rgba) return fail(ctx, VPL_ERR_INVALID_ARG, "bad batch arrays");
+    if (n_views > (1 << 22)) return fail(ctx, VPL_ERR_INVALID_ARG, "a batch holds at most 2^22 views");
     if (tile_w != 0 && tile_w != 4 && tile_w != 8 && tile_w != 16 && tile_w != 32)
         return fail(ctx, VPL_ERR_INVALID_ARG, "tile_w must be 0, 4, 8, 16 or 32");
     int fmt = gbufs[0].format;

@@ -315,9 +315,10 @@ static GatherExtra single_view_extra(const GatherArgs &a, int *counter)
 // VPL order of a gather.  The image is the same sum in any order (up to FP32
 // rounding); the order only steers speed: consecutive VPLs close in space
 // send each warp's shadow packets through the same part of the BVH and let
-// the per-pixel occluder cache hit.  Order = 30-bit Morton code of the VPL
-// position in the scene box, ties by index (a stable sort); in a batch each
-// view's VPLs are ordered on their own (view index above the code).
+// the per-pixel occluder cache hit.  Order = 42-bit Morton code (14 bits per
+// axis) of the VPL position in the scene box, ties by index (a stable sort);
+// in a batch each view's VPLs are ordered on their own (view index above the
+// code).
 // ---------------------------------------------------------------------------
 __global__ void vpl_order_keys_kernel(const double *gbox, const float4 *v_pos, const ViewDesc *views, int n_views,
                                       int64_t total, uint64_t *keys, uint32_t *vals)
@@ -343,9 +344,9 @@ __global__ void vpl_order_keys_kernel(const double *gbox, const float4 *v_pos, c
     for (int a = 0; a < 3; a++) {
         const float lo = (float)gbox[a], ext = (float)gbox[3 + a] - lo;
         const float u = ext > 0.0f ? (c[a] - lo) / ext : 0.0f;
-        q[a] = (uint32_t)fminf(fmaxf(floorf(u * 1024.0f), 0.0f), 1023.0f);
+        q[a] = (uint32_t)fminf(fmaxf(floorf(u * 16384.0f), 0.0f), 16383.0f);
     }
-    keys[g] = ((uint64_t)view << 32) | morton63(q[0], q[1], q[2]);
+    keys[g] = ((uint64_t)view << 42) | morton63(q[0], q[1], q[2]);
     vals[g] = (uint32_t)local;
 }
 
@@ -358,8 +359,8 @@ static cudaError_t vpl_order(const Exec &ex, const SceneView &s, const float4 *v
     vpl_order_keys_kernel<<<grid_for(total, 256), 256, 0, ex.stream>>>(s.gbox, v_pos, views, n_views, total,
                                                                        keys.as<uint64_t>(), order.as<uint32_t>());
     VPL_LAUNCHED(ex);
-    int bits = 32;
-    while (bits < 64 && ((int64_t)1 << (bits - 32)) < n_views) bits++;
+    int bits = 42;
+    while (bits < 64 && ((int64_t)1 << (bits - 42)) < n_views) bits++;
     return radix_sort_pairs(ex, keys.as<uint64_t>(), order.as<uint32_t>(), nullptr, total, bits);
 }
 
