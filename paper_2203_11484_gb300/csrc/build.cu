@@ -573,6 +573,126 @@ __global__ void ploc_ctl_kernel(PlocCtl *ctl, const unsigned long long *off)
     ctl->n_cur = (int)(tot >> 32);
 }
 
+// The last passes, from at most kTailMax clusters down to one, in a single
+// block: the same three steps per pass (nearest neighbours, mutual-pair
+// flags with a block scan, merge and compaction), with block barriers in
+// place of kernel boundaries.
+constexpr int kTailThreads = 1024, kTailItems = 4, kTailMax = kTailThreads * kTailItems;
+
+__global__ void __launch_bounds__(kTailThreads) ploc_tail_kernel(int T, PlocCtl *ctl, int cur, int *cref0,
+                                                                 float *cbox0, int *cref1, float *cbox1, int *nn,
+                                                                 int *child, float *nodebox, int *parent_int,
+                                                                 int *parent_leaf)
+{
+    __shared__ int wk[kTailThreads / 32], wm[kTailThreads / 32];
+    __shared__ int tot[2];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int n = ctl->n_cur, made = ctl->node_next;
+    for (int pass = 0; n > 1 && pass < kTailMax; pass++) { // each pass merges at least one pair
+        const int *rin = cur ? cref1 : cref0;
+        const float *bin = cur ? cbox1 : cbox0;
+        int *rout = cur ? cref0 : cref1;
+        float *bout = cur ? cbox0 : cbox1;
+        for (int i = tid; i < n; i += kTailThreads) {
+            const float *bi = bin + 6 * (int64_t)i;
+            const int j0 = max(0, i - kPlocR), j1 = min(n - 1, i + kPlocR);
+            int bj = j0 == i ? i + 1 : j0;
+            float best = union_area(bi, bin + 6 * (int64_t)bj);
+            for (int j = bj + 1; j <= j1; j++) {
+                if (j == i) continue;
+                const float a = union_area(bi, bin + 6 * (int64_t)j);
+                if (a < best) {
+                    best = a;
+                    bj = j;
+                }
+            }
+            nn[i] = bj;
+        }
+        __syncthreads();
+        // items tid * kTailItems + k, in order: flags and their block scan
+        int keep[kTailItems], make[kTailItems], sk = 0, sm = 0;
+        for (int k = 0; k < kTailItems; k++) {
+            const int i = tid * kTailItems + k;
+            keep[k] = make[k] = 0;
+            if (i < n) {
+                const int j = nn[i];
+                const bool mutual = nn[j] == i;
+                make[k] = mutual && i < j;
+                keep[k] = !(mutual && i > j);
+            }
+            sk += keep[k];
+            sm += make[k];
+        }
+        int ik = sk, im = sm;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(kFull, ik, o), b = __shfl_up_sync(kFull, im, o);
+            if (lane >= o) {
+                ik += a;
+                im += b;
+            }
+        }
+        if (lane == 31) {
+            wk[w] = ik;
+            wm[w] = im;
+        }
+        __syncthreads();
+        if (w == 0) {
+            int a = wk[lane], b = wm[lane]; // kTailThreads / 32 == 32 warps
+            int ia = a, ib = b;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(kFull, ia, o), y = __shfl_up_sync(kFull, ib, o);
+                if (lane >= o) {
+                    ia += x;
+                    ib += y;
+                }
+            }
+            wk[lane] = ia - a;
+            wm[lane] = ib - b;
+            if (lane == 31) {
+                tot[0] = ia;
+                tot[1] = ib;
+            }
+        }
+        __syncthreads();
+        int pk = wk[w] + ik - sk, pm = wm[w] + im - sm; // exclusive offsets of this thread's first item
+        for (int k = 0; k < kTailItems; k++) {
+            const int i = tid * kTailItems + k;
+            if (i < n && keep[k]) {
+                if (make[k]) {
+                    const int j = nn[i];
+                    const int id = (T - 2) - (made + pm);
+                    const int a = rin[i], b = rin[j];
+                    child[2 * (int64_t)id] = a;
+                    child[2 * (int64_t)id + 1] = b;
+                    if (a < 0) parent_leaf[~a] = id; else parent_int[a] = id;
+                    if (b < 0) parent_leaf[~b] = id; else parent_int[b] = id;
+                    const float *p = bin + 6 * (int64_t)i, *q = bin + 6 * (int64_t)j;
+                    float *o = nodebox + 6 * (int64_t)id, *c = bout + 6 * (int64_t)pk;
+                    for (int x = 0; x < 3; x++) {
+                        o[x] = c[x] = fminf(p[x], q[x]);
+                        o[3 + x] = c[3 + x] = fmaxf(p[3 + x], q[3 + x]);
+                    }
+                    rout[pk] = id;
+                } else {
+                    rout[pk] = rin[i];
+                    for (int x = 0; x < 6; x++) bout[6 * (int64_t)pk + x] = bin[6 * (int64_t)i + x];
+                }
+            }
+            pk += keep[k];
+            pm += make[k];
+        }
+        __syncthreads();
+        n = tot[0];
+        made += tot[1];
+        cur ^= 1;
+        __syncthreads(); // tot is rewritten by the next pass
+    }
+    if (tid == 0) {
+        ctl->n_cur = n;
+        ctl->node_next = made;
+    }
+}
+
 // Runs merge passes until one cluster is left; *done stays false if a check
 // sees no merge over a whole batch of passes (only non-finite boxes can do
 // that), and the caller then builds the Karras hierarchy instead.
@@ -596,21 +716,31 @@ static cudaError_t ploc_build(const Exec &ex, int T, const float *leafbox, int *
     VPL_LAUNCHED(ex);
     int cur = 0, left = T;
     while (left > 1) {
-        for (int it = 0; it < kBatch; it++) {
-            ploc_nn_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(c, cbox[cur].as<float>(), nn.as<int>());
+        if (left <= kTailMax) {
+            ploc_tail_kernel<<<1, kTailThreads, 0, ex.stream>>>(T, c, cur, cref[0].as<int>(), cbox[0].as<float>(),
+                                                               cref[1].as<int>(), cbox[1].as<float>(), nn.as<int>(),
+                                                               child, nodebox, parent_int, parent_leaf);
             VPL_LAUNCHED(ex);
-            ploc_flags_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(c, nn.as<int>(), flags.as<unsigned long long>());
-            VPL_LAUNCHED(ex);
-            VPL_TRY(exclusive_scan<unsigned long long>(ex, flags.as<unsigned long long>(),
-                                                       off.as<unsigned long long>(), &c->n_cur, T));
-            ploc_merge_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(
-                T, c, nn.as<int>(), flags.as<unsigned long long>(), off.as<unsigned long long>(), cref[cur].as<int>(),
-                cbox[cur].as<float>(), cref[1 - cur].as<int>(), cbox[1 - cur].as<float>(), child, nodebox,
-                parent_int, parent_leaf);
-            VPL_LAUNCHED(ex);
-            ploc_ctl_kernel<<<1, 1, 0, ex.stream>>>(c, off.as<unsigned long long>());
-            VPL_LAUNCHED(ex);
-            cur = 1 - cur;
+        } else {
+            // grids sized by the last count read back (an upper bound)
+            const unsigned g = grid_for(left, B);
+            for (int it = 0; it < kBatch; it++) {
+                ploc_nn_kernel<<<g, B, 0, ex.stream>>>(c, cbox[cur].as<float>(), nn.as<int>());
+                VPL_LAUNCHED(ex);
+                ploc_flags_kernel<<<g, B, 0, ex.stream>>>(c, nn.as<int>(), flags.as<unsigned long long>());
+                VPL_LAUNCHED(ex);
+                VPL_TRY(exclusive_scan<unsigned long long>(ex, flags.as<unsigned long long>(),
+                                                           off.as<unsigned long long>(), &c->n_cur, left));
+                ploc_merge_kernel<<<g, B, 0, ex.stream>>>(T, c, nn.as<int>(), flags.as<unsigned long long>(),
+                                                          off.as<unsigned long long>(), cref[cur].as<int>(),
+                                                          cbox[cur].as<float>(), cref[1 - cur].as<int>(),
+                                                          cbox[1 - cur].as<float>(), child, nodebox, parent_int,
+                                                          parent_leaf);
+                VPL_LAUNCHED(ex);
+                ploc_ctl_kernel<<<1, 1, 0, ex.stream>>>(c, off.as<unsigned long long>());
+                VPL_LAUNCHED(ex);
+                cur = 1 - cur;
+            }
         }
         int now = 0;
         VPL_TRY(cudaMemcpyAsync(&now, &c->n_cur, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
