@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
         float4 gn = valid ? load_attr(g_nrm, p, gfmt) : make_float4(0, 0, 0, 0);
         const float3 y = f3(gp), ny = f3(gn);
         const float3 o = fma3(ny, eps, y);
-        int occ_cache = -1;                    // last blocking triangle of this pixel
+        int occ_cache = -1, occ_cache2 = -1;   // last blocking triangles of this pixel
         float ax = 0.0f, ay = 0.0f, az = 0.0f; // running sums
         float cx = 0.0f, cy_ = 0.0f, cz = 0.0f; // Kahan compensation
         for (int base = 0; base < M; base += 32) {
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                 bool vis = true;
                 if (VIS == VPL_VIS_BVH) {
                     const float3 q = fma3(f3(xn), eps, f3(xp));
-                    vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), occ_cache, stack[wid], status, wc);
+                    vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), occ_cache, occ_cache2, stack[wid], status, wc);
                 } else if (VIS == VPL_VIS_BRUTE) {
                     const float3 q = fma3(f3(xn), eps, f3(xp));
                     vis = !warp_occluded_brute<COUNT>(s, want, make_ray(o, q - o), wc);

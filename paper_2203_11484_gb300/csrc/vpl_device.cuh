@@ -464,14 +464,14 @@ struct WarpCounters {
     uint32_t steps;         // per warp: packet traversal steps (same in every lane)
 };
 
-// `cache` (per lane) is the leaf-order slot of the triangle that last blocked
-// one of this lane's segments, or -1.  It is tested before the traversal:
-// neighbouring VPLs are usually hidden by the same triangle.  The answer is
-// the same with or without it (a segment is blocked when any triangle blocks
-// it).
+// `cache`, `cache2` (per lane) are the triangle slots of the last two
+// triangles that blocked one of this lane's segments (most recent first), or
+// -1.  They are tested before the traversal: neighbouring VPLs are usually
+// hidden by the same triangle.  The answer is the same with or without them
+// (a segment is blocked when any triangle blocks it).
 template <bool COUNT>
 __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, const Ray &r, int &cache,
-                                              int *stk, int *status, WarpCounters &wc)
+                                              int &cache2, int *stk, int *status, WarpCounters &wc)
 {
     const int lane = threadIdx.x & 31;
     bool occl = false;
@@ -481,6 +481,15 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
         if (tri_hit(r, __ldg(s.tri + 3 * cache), __ldg(s.tri + 3 * cache + 1), __ldg(s.tri + 3 * cache + 2), t) &&
             t > 0.0f && t < 1.0f)
             occl = true;
+    }
+    if (want && !occl && cache2 >= 0) {
+        float t;
+        if (COUNT) wc.tests++;
+        if (tri_hit(r, __ldg(s.tri + 3 * cache2), __ldg(s.tri + 3 * cache2 + 1), __ldg(s.tri + 3 * cache2 + 2), t) &&
+            t > 0.0f && t < 1.0f) {
+            occl = true;
+            const int x = cache; cache = cache2; cache2 = x;
+        }
     }
     unsigned alive = __ballot_sync(kFull, want && !occl);
     if (alive == 0) return occl;
@@ -546,6 +555,7 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
                     if (tri_hit(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2), t) &&
                         t > 0.0f && t < 1.0f) {
                         occl = true;
+                        cache2 = cache;
                         cache = q;
                     }
                 }
