@@ -99,6 +99,8 @@ def lib() -> C.CDLL:
                                      C.c_double, C.c_double, C.c_int32, _D]
             L.orc_pairs.argtypes = [_P, _D, _D, C.c_int64, _D, _D, C.c_double, C.c_double,
                                     C.c_int32, _U8, _D, C.POINTER(C.c_int8), _D]
+            L.orc_light_vpls.argtypes = [C.POINTER(_Light), C.c_int64, C.c_uint64, _D, _D, _D, _I64]
+            L.orc_light_vpls.restype = C.c_int64
             L.orc_num_threads.restype = C.c_int32
             _lib = L
     return _lib
@@ -243,6 +245,19 @@ class OracleScene:
                     n_close=info.n_close, shift_s=info.shift_s, f_total=int(info.f_total),
                     paths=info.paths, m_far_kept=info.m_far_kept, a_rep=info.a_rep,
                     status=info.status)
+
+    def light_vpls(self, n: int, seed: int) -> dict:
+        """Direct term of Eq. 1 as n light-sample VPLs (orc_light_vpls);
+        None for a point light."""
+        pos = np.zeros((max(n, 1), 3))
+        nrm = np.zeros((max(n, 1), 3))
+        flux = np.zeros((max(n, 1), 3))
+        tag = np.zeros(max(n, 1), np.int64)
+        r = lib().orc_light_vpls(C.byref(self.light), int(n), C.c_uint64(seed), _ptr(pos, C.c_double),
+                                 _ptr(nrm, C.c_double), _ptr(flux, C.c_double), _ptr(tag, C.c_int64))
+        if r < 0:
+            return None
+        return dict(pos=pos[:n], nrm=nrm[:n], flux=flux[:n], tag=tag[:n], tri=np.full(n, -1, np.int64))
 
     def gbuffer(self, cam, pixels=None, vis_mode=0) -> dict:
         if pixels is None:

@@ -91,7 +91,7 @@ ORC_API void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uin
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-enum { STREAM_PATCH = 1, STREAM_LIGHT = 2, STREAM_IR = 3 };
+enum { STREAM_PATCH = 1, STREAM_LIGHT = 2, STREAM_IR = 3, STREAM_DIRECT = 4 };
 
 static void rng4(uint64_t seed, uint64_t stream, uint64_t i, uint64_t j, uint64_t w[4])
 {
@@ -530,6 +530,34 @@ static d3 light_point(const olight *L, double s1, double s2)
     d3 a = scl(ld3(L->edge_u), (2.0 * s1 - 1.0) * 0.5);
     d3 b = scl(ld3(L->edge_v), (2.0 * s2 - 1.0) * 0.5);
     return add(add(c, a), b);
+}
+
+/* Direct term L_e(y) of Eq. 1 as light-sample VPLs: sample s is the point
+ * of the square light at Philox (seed, STREAM_DIRECT) counter (s, 0) words
+ * w0, w1 -> (s1, s2), with the light's normal and power P / S.  Gathered
+ * with Eq. 1's sum, S such VPLs give the Monte Carlo estimate
+ * (rho/pi) * (1/S) sum_s P cos_i cos_y / (pi d^2) V of the light's one-sided
+ * Lambertian emission (radiance P / (pi A_L)) reflected at y.  Tag -1 - s.
+ * Returns -1 for a point light (no normal: its direct term is not this sum). */
+ORC_API int64_t orc_light_vpls(const olight *L, int64_t S, uint64_t seed, double *pos, double *nrm, double *flux,
+                               int64_t *tag)
+{
+    if (L->type == 1) return -1;
+    d3 nl = ld3(L->normal);
+    for (int64_t k = 0; k < S; k++) {
+        uint64_t w[4];
+        rng4(seed, STREAM_DIRECT, (uint64_t)k, 0, w);
+        d3 y = light_point(L, u01(w[0]), u01(w[1]));
+        pos[3 * k] = y.x;
+        pos[3 * k + 1] = y.y;
+        pos[3 * k + 2] = y.z;
+        nrm[3 * k] = nl.x;
+        nrm[3 * k + 1] = nl.y;
+        nrm[3 * k + 2] = nl.z;
+        for (int c = 0; c < 3; c++) flux[3 * k + c] = L->power[c] / (double)S;
+        tag[k] = -1 - k;
+    }
+    return S;
 }
 
 /* orthonormal basis around unit n (Duff et al., JCGT 2017) */

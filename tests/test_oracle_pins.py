@@ -511,3 +511,57 @@ def test_pipeline_counts_tiny(orc):
     # brute-force and BVH visibility give the same image on the tiny scene
     r0 = orc.render(o, v, vis_mode=0)
     assert np.array_equal(r0["image"], r["image"])
+
+
+# ---------------------------------------------------------------------------
+# direct term L_e(y) of Eq. 1: light-sample VPLs, gathered like the others
+# ---------------------------------------------------------------------------
+def _square_light(power=(2.0, 1.5, 1.0)):
+    return W.Light(center=(0.1, 0.2, 1.0), normal=(0, 0, -1), edge_u=(0.4, 0.0, 0.0), edge_v=(0.0, 0.4, 0.0),
+                   power=power, type=W.LIGHT_AREA)
+
+
+def test_light_vpls_follow_philox_and_split_the_power(orc):
+    """Sample s: point (2 s1 - 1) eu/2 + (2 s2 - 1) ev/2 from the centre with
+    s1, s2 the top 24 bits of Philox words 0, 1 at key (seed, 4), counter
+    (s, 0, 0, 0) -- numpy's Philox gives the words; flux P / S each."""
+    light = _square_light()
+    o = orc.OracleScene(plane_scene(light=light))
+    S, seed = 257, 11
+    v = o.light_vpls(S, seed)
+    f = lambda a: np.array(a, np.float32).astype(np.float64)  # the light is given in FP32
+    c, eu, ev = f(light.center), f(light.edge_u), f(light.edge_v)
+    for s in range(S):
+        w = _numpy_philox_block((s, 0, 0, 0), (seed, 4))
+        s1, s2 = (int(w[0]) >> 40) / 2.0**24, (int(w[1]) >> 40) / 2.0**24
+        want = c + (2 * s1 - 1) * 0.5 * eu + (2 * s2 - 1) * 0.5 * ev
+        assert np.allclose(v["pos"][s], want, rtol=0, atol=1e-15)
+    assert np.array_equal(v["nrm"], np.tile([0.0, 0.0, -1.0], (S, 1)))
+    assert np.array_equal(v["tag"], -1 - np.arange(S))
+    assert np.allclose(v["flux"].sum(0), f(light.power), rtol=1e-12)
+    pt = W.Light(center=(0, 0, 1), normal=(0, 0, -1), edge_u=(0, 0, 0), edge_v=(0, 0, 0), power=(1, 1, 1),
+                 type=W.LIGHT_POINT)
+    assert orc.OracleScene(plane_scene(light=pt)).light_vpls(4, 1) is None
+
+
+def test_direct_term_matches_lambert(orc):
+    """Gathering the light samples over an unoccluded plane gives rho/pi times
+    Lambert's closed-form irradiance of the square emitter (radiance
+    P / (pi A_L)), within the Monte Carlo error; a receiver facing away or
+    behind the emitter's plane gets nothing."""
+    light = _square_light(power=(2.0, 2.0, 2.0))
+    o = orc.OracleScene(plane_scene(half=100.0, albedo=0.6, light=light))
+    v = o.light_vpls(40000, 7)
+    xs = np.array([[0.1, 0.2, 0.0], [0.6, -0.3, 0.0], [-1.5, 1.0, 0.0], [3.0, 0.2, 0.0]])
+    gb = dict(pos=xs, nrm=np.tile([0, 0, 1.0], (len(xs), 1)), rho=np.full((len(xs), 3), 0.6),
+              tri=np.zeros(len(xs), np.int64))
+    out = o.gather(gb, v, d2_min=1e-12, eps=1e-9, vis_mode=1)
+    c, eu, ev = np.array(light.center), np.array(light.edge_u), np.array(light.edge_v)
+    poly = [c - eu / 2 - ev / 2, c + eu / 2 - ev / 2, c + eu / 2 + ev / 2, c - eu / 2 + ev / 2]
+    Lrad = 2.0 / (math.pi * 0.16)
+    for k, x in enumerate(xs):
+        want = 0.6 / math.pi * _lambert_irradiance(x, np.array([0, 0, 1.0]), poly, Lrad)
+        assert abs(out[k, 0] - want) < 0.02 * want, (k, out[k, 0], want)
+    away = dict(pos=np.array([[0.1, 0.2, 0.0], [0.1, 0.2, 2.0]]), nrm=np.array([[0, 0, -1.0], [0, 0, 1.0]]),
+                rho=np.full((2, 3), 0.6), tri=np.zeros(2, np.int64))
+    assert np.array_equal(o.gather(away, v, d2_min=1e-12, eps=1e-9, vis_mode=1), np.zeros((2, 3)))
