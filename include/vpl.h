@@ -204,6 +204,20 @@ VPL_API int vpl_generate(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam
  * streams, whichever of them wrote its record last). */
 VPL_API int vpl_generate_info(vpl_ctx *ctx, vpl_gen_info *out);
 
+/* Direct term L_e(y) of Eq. 1 (the light's own contribution, which the VPL
+ * sum leaves out) as n light-sample VPLs written to vpls (count == n, either
+ * format): sample k is the point c + (2 s1 - 1) edge_u / 2 + (2 s2 - 1)
+ * edge_v / 2 of the scene's square light, with s1, s2 the top 24 bits of
+ * Philox4x64-10 words 0 and 1 at key (seed, 4), counter (k, 0, 0, 0), the
+ * light's normal, flux power / n and tag -1 - k.  vpl_gather of these rows
+ * gives (rho/pi) (1/n) sum_k power cos_k cos_y V / (pi d^2), the Monte Carlo
+ * estimate of the one-sided Lambertian emitter (radiance power / (pi A))
+ * reflected at y; gathering them together with the indirect VPLs (rows of
+ * one set) gives the composite L(y) of Eq. 1.  A point light has no
+ * emitting normal for this sum: VPL_ERR_UNSUPPORTED. */
+VPL_API int vpl_light_vpls(vpl_ctx *ctx, vpl_scene_id scene, int32_t n, uint64_t seed,
+                           const vpl_vpl_set *vpls, vpl_stream stream);
+
 /* Step (4): out_rgba (device float4[width*height]) receives, per pixel,
  * (rho/pi) * sum_i flux_i cos_i cos_y / (pi max(d^2, d2_min)) * V_i.
  * The sum runs over the VPLs in the Morton order of their positions (a

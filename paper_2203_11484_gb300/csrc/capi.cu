@@ -477,6 +477,24 @@ int vpl_generate(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const 
     return VPL_OK;
 }
 
+int vpl_light_vpls(vpl_ctx *ctx, vpl_scene_id scene, int32_t n, uint64_t seed, const vpl_vpl_set *vpls,
+                   vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    int rc = check_vpls(ctx, vpls);
+    if (rc) return rc;
+    if (n < 0 || vpls->count != n) return fail(ctx, VPL_ERR_INVALID_ARG, "vpl set count must equal n >= 0");
+    if (s->light.type != VPL_LIGHT_AREA)
+        return fail(ctx, VPL_ERR_UNSUPPORTED, "light samples need an area light (a point light has no normal)");
+    DeviceGuard g(ctx->device);
+    CK(ctx, light_vpls(exec_of(ctx, stream), light_of(s->light), n, seed, (float4 *)vpls->pos, vpls->nrm, vpls->flux,
+                       vpls->format),
+       "vpl_light_vpls");
+    return VPL_OK;
+}
+
 int vpl_generate_info(vpl_ctx *ctx, vpl_gen_info *out)
 {
     if (!ctx || !out) return VPL_ERR_INVALID_ARG;

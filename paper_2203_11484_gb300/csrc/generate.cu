@@ -340,6 +340,34 @@ __global__ void far_tail_kernel(GenArgs g, const GenInfoDev *info, float4 *pos, 
     store_vpl(pos, nrm, flux, g.m_close + i, z, -1, z, -1, z, fmt);
 }
 
+// Direct term L_e(y) of Eq. 1 as light-sample VPLs: sample k is the point of
+// the square light at Philox (seed, stream 4) counter (k, 0) words 0 and 1,
+// with the light's normal and power P / n; tag -1 - k.  Gathered like the
+// indirect VPLs, n of them estimate the light's one-sided Lambertian emission
+// reflected at each pixel.
+__global__ void light_vpls_kernel(LightView L, int n, uint64_t seed, float4 *pos, void *nrm, void *flux, int fmt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint64_t w[4];
+    rng4(seed, kStreamDirect, (uint64_t)k, 0, w);
+    const D3 y = light_point(L, u01(w[0]), u01(w[1]));
+    store_vpl(pos, nrm, flux, k, make_float3((float)y.x, (float)y.y, (float)y.z), -1,
+              make_float3(L.normal[0], L.normal[1], L.normal[2]), -1 - k,
+              make_float3((float)((double)L.power[0] / n), (float)((double)L.power[1] / n),
+                          (float)((double)L.power[2] / n)),
+              fmt);
+}
+
+cudaError_t light_vpls(const Exec &ex, const LightView &L, int n, uint64_t seed, float4 *pos, void *nrm, void *flux,
+                       int fmt)
+{
+    if (n <= 0) return cudaSuccess;
+    light_vpls_kernel<<<grid_for(n, 256), 256, 0, ex.stream>>>(L, n, seed, pos, nrm, flux, fmt);
+    VPL_LAUNCHED(ex);
+    return cudaSuccess;
+}
+
 cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, float4 *pos, void *nrm,
                           void *flux, int fmt, GenInfoDev *report)
 {

@@ -100,6 +100,8 @@ struct GenInfoDev {
 
 cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, float4 *pos,
                           void *nrm, void *flux, int format, GenInfoDev *report);
+cudaError_t light_vpls(const Exec &ex, const LightView &L, int n, uint64_t seed, float4 *pos, void *nrm, void *flux,
+                       int fmt);
 
 // ---- gather.cu -----------------------------------------------------------------
 struct CamArgs {

@@ -89,6 +89,7 @@ _SIGS = {
     "vpl_scene_release": (C.c_int, [_P, C.c_uint64]),
     "vpl_scene_query": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_scene_info)]),
     "vpl_gbuffer_build": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_camera), C.POINTER(vpl_gbuffer), _P]),
+    "vpl_light_vpls": (C.c_int, [_P, C.c_uint64, C.c_int32, C.c_uint64, C.POINTER(vpl_vpl_set), _P]),
     "vpl_generate": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_camera), C.POINTER(vpl_gen_params),
                                C.POINTER(vpl_vpl_set), _P]),
     "vpl_generate_info": (C.c_int, [_P, C.POINTER(vpl_gen_info)]),
@@ -256,6 +257,12 @@ class VplSet:
         s.count, s.format = self.count, self.format
         return s
 
+    def rows(self, first: int, count: int) -> "VplSet":
+        """Rows [first, first + count) of this set (views, no copy): e.g. the
+        indirect VPLs and the light samples of the direct term in one set."""
+        return VplSet(self.pos[first:first + count], self.nrm[first:first + count],
+                      self.flux[first:first + count], self.format)
+
 
 # ---- the C entry points ----------------------------------------------------------------
 def vpl_create(device: int = 0) -> C.c_void_p:
@@ -298,6 +305,12 @@ def vpl_gbuffer_build(ctx, scene: int, camera: W.Camera, gbuf: GBuffer, stream=N
     cam, gb = make_camera(camera), gbuf.struct()
     _check(ctx, load().vpl_gbuffer_build(ctx, scene, C.byref(cam), C.byref(gb), _stream(stream)),
            "vpl_gbuffer_build")
+
+
+def vpl_light_vpls(ctx, scene: int, n: int, seed: int, vpls: VplSet, stream=None) -> None:
+    vs = vpls.struct()
+    _check(ctx, load().vpl_light_vpls(ctx, scene, int(n), C.c_uint64(seed), C.byref(vs), _stream(stream)),
+           "vpl_light_vpls")
 
 
 def vpl_generate(ctx, scene: int, camera: W.Camera, gen: W.GenParams, vpls: VplSet, stream=None) -> None:
