@@ -477,6 +477,33 @@ def run_ours(args):
         "achieved": v1_tflops, "frac": v1_tflops / peak_tflops,
         "frac_at_median_clock": v1_tflops / (sms * 128 * 2 * med_mhz * 1e6 / 1e12)}
     roofline["frac_at_median_clock"] = achieved / (sms * 128 * 2 * med_mhz * 1e6 / 1e12)
+
+    # ---- direct term (Eq. 1's L_e(y)) as light-sample VPLs, composite image ----
+    # reported beside the metric, which counts the indirect VPLs only
+    direct = None
+    if sc.light.type == W.LIGHT_AREA:
+        n_light = 256
+        both = V.VplSet.empty(M + n_light, fmt=fmt)
+        V.vpl_generate(ctx.h, sid, cam, gen, both.rows(0, M), stream)
+        V.vpl_light_vpls(ctx.h, sid, n_light, 1, both.rows(M, n_light), stream)
+        times = {}
+        for name, part in (("direct", both.rows(M, n_light)), ("composite", both)):
+            ms = []
+            for k in range(3):
+                flush.fill_(float(k))
+                e0, e1 = mk(), mk()
+                e0.record(stream)
+                V.vpl_gather(ctx.h, sid, gb, part, gat, out, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k:
+                    ms.append(e0.elapsed_time(e1))
+            times[name] = statistics.mean(ms)
+        V.vpl_sync(ctx.h, stream)
+        direct = {"light_vpls": n_light, "direct_gather_ms": times["direct"],
+                  "direct_pairs_per_s": npx * n_light / (times["direct"] / 1e3),
+                  "composite_vpls": M + n_light, "composite_gather_ms": times["composite"],
+                  "composite_pairs_per_s": npx * (M + n_light) / (times["composite"] / 1e3)}
     V.vpl_scene_release(ctx.h, sid)
 
     # ---- end to end: host buffers in, image out, through the same API -----
@@ -534,7 +561,7 @@ def run_ours(args):
                 "views_per_s": ws * args.steps / (total_ms / 1e3),
                 "gather_ms_per_step": gather_in_step_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk, "wall_s": wall, "batch": batch,
+                "gpu_launches": int(launches), "clocks": clk, "wall_s": wall, "direct_term": direct, "batch": batch,
                 "serving": serving}
         print(json.dumps(line), flush=True)
     ctx.close()
