@@ -55,7 +55,7 @@ class _Gen(C.Structure):
     _fields_ = [("d_close", C.c_double), ("ray_eps", C.c_double), ("ir_max_paths", C.c_int64),
                 ("seed", C.c_uint64), ("m_close", C.c_int32), ("m_far", C.c_int32),
                 ("max_bounces", C.c_int32), ("light_samples", C.c_int32),
-                ("vis_mode", C.c_int32)]
+                ("vis_mode", C.c_int32), ("close_rule", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -88,7 +88,7 @@ def lib() -> C.CDLL:
             L.orc_occluded_batch.argtypes = [_P, C.c_int64, _D, _D, C.c_int32, _U8]
             L.orc_segment_margin.argtypes = [_P, _D, _D]
             L.orc_segment_margin.restype = C.c_double
-            L.orc_classify.argtypes = [_P, C.POINTER(_Cam), C.POINTER(_Light), C.c_double, _U8]
+            L.orc_classify.argtypes = [_P, C.POINTER(_Cam), C.POINTER(_Light), C.c_double, C.c_int32, _U8]
             L.orc_classify.restype = C.c_int64
             L.orc_generate.argtypes = [_P, C.POINTER(_Cam), C.POINTER(_Light), C.POINTER(_Gen),
                                        _D, _D, _D, _I64, _I64, C.POINTER(_Info)]
@@ -159,6 +159,7 @@ def gen_struct(gen, vis_mode: int) -> _Gen:
     g.m_close, g.m_far = int(gen.m_close), int(gen.m_far)
     g.max_bounces, g.light_samples = int(gen.max_bounces), int(gen.light_samples)
     g.vis_mode = int(vis_mode)
+    g.close_rule = int(getattr(gen, "close_rule", 0))
     return g
 
 
@@ -221,10 +222,10 @@ class OracleScene:
         return float(lib().orc_segment_margin(self.h, _ptr(p, C.c_double), _ptr(q, C.c_double)))
 
     # --- the method --------------------------------------------------------
-    def classify(self, cam, d_close) -> np.ndarray:
+    def classify(self, cam, d_close, rule: int = 0) -> np.ndarray:
         flags = np.zeros(self.scene.n_tris, np.uint8)
         c = cam_struct(cam)
-        lib().orc_classify(self.h, C.byref(c), C.byref(self.light), float(d_close),
+        lib().orc_classify(self.h, C.byref(c), C.byref(self.light), float(d_close), int(rule),
                            _ptr(flags, C.c_uint8))
         return flags.astype(bool)
 

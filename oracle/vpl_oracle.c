@@ -136,7 +136,7 @@ typedef struct {
 
 typedef struct {
     int64_t nt;
-    d3 *a, *e1, *e2, *cr, *n, *g;
+    d3 *a, *b, *c, *e1, *e2, *cr, *n, *g;
     double *area, *rho;
     d3 glo, ghi;           /* AABB of all centroids   */
     d3 vlo, vhi;           /* AABB of all vertices    */
@@ -163,6 +163,7 @@ typedef struct {
     uint64_t seed;
     int32_t m_close, m_far, max_bounces, light_samples;
     int32_t vis_mode;      /* 0 BVH, 1 brute force */
+    int32_t close_rule;    /* 0 centroid, 1 centroid or any vertex (see is_close) */
 } ogen;
 
 /* ---- FP64 BVH: top-down median split, boxes padded so that the set of
@@ -223,6 +224,7 @@ ORC_API void *orc_scene_create(const float *verts, int64_t nv, const int32_t *tr
     oscene *s = (oscene *)calloc(1, sizeof(oscene));
     s->nt = nt;
     s->a = malloc(sizeof(d3) * nt);   s->e1 = malloc(sizeof(d3) * nt);
+    s->b = malloc(sizeof(d3) * nt);   s->c = malloc(sizeof(d3) * nt);
     s->e2 = malloc(sizeof(d3) * nt);  s->cr = malloc(sizeof(d3) * nt);
     s->n = malloc(sizeof(d3) * nt);   s->g = malloc(sizeof(d3) * nt);
     s->area = malloc(sizeof(double) * nt);
@@ -236,7 +238,7 @@ ORC_API void *orc_scene_create(const float *verts, int64_t nv, const int32_t *tr
         d3 e1 = sub(b, a), e2 = sub(c, a);
         d3 cr = cross(e1, e2);
         double l = len(cr);
-        s->a[t] = a; s->e1[t] = e1; s->e2[t] = e2; s->cr[t] = cr;
+        s->a[t] = a; s->b[t] = b; s->c[t] = c; s->e1[t] = e1; s->e2[t] = e2; s->cr[t] = cr;
         s->n[t] = l > 0.0 ? mk(cr.x / l, cr.y / l, cr.z / l) : mk(0, 0, 0);
         s->area[t] = 0.5 * l;
         d3 g = add(add(a, b), c);
@@ -265,7 +267,7 @@ ORC_API void orc_scene_destroy(void *p)
 {
     oscene *s = (oscene *)p;
     if (!s) return;
-    free(s->a); free(s->e1); free(s->e2); free(s->cr); free(s->n); free(s->g);
+    free(s->a); free(s->b); free(s->c); free(s->e1); free(s->e2); free(s->cr); free(s->n); free(s->g);
     free(s->area); free(s->rho); free(s->nodes); free(s->perm);
     free(s);
 }
@@ -487,26 +489,36 @@ static frame cam_frame(const ocamera *c)
     return F;
 }
 
-/* close/distant split: a one-sided face is close range when it faces the
- * camera, lies inside the field of view and nearer than d_close; patch
- * sampling further only considers faces that face the light. */
-static int is_close(const oscene *s, int64_t t, const frame *F, const olight *L, double dc2)
+/* point p inside the field of view and nearer than d_close */
+static int in_view(d3 p, const frame *F, double dc2)
 {
-    d3 g = s->g[t], cr = s->cr[t];
-    if (!(dot(cr, sub(F->e, g)) > 0.0)) return 0;
-    d3 v = sub(g, F->e);
+    d3 v = sub(p, F->e);
     double z = dot(v, F->f);
     if (!(z > 0.0)) return 0;
     if (!(fabs(dot(v, F->r)) <= z * F->th)) return 0;
     if (!(fabs(dot(v, F->u)) <= z * F->tv)) return 0;
-    if (!(dot(v, v) < dc2)) return 0;
+    return dot(v, v) < dc2;
+}
+
+/* close/distant split: a one-sided face is close range when it faces the
+ * camera, lies inside the field of view and nearer than d_close -- judged at
+ * its centroid (rule 0), or at its centroid or any of its vertices (rule 1,
+ * the any-vertex reading of "within the field of view") -- and patch
+ * sampling further only considers faces that face the light. */
+static int is_close(const oscene *s, int64_t t, const frame *F, const olight *L, double dc2, int rule)
+{
+    d3 g = s->g[t], cr = s->cr[t];
+    if (!(dot(cr, sub(F->e, g)) > 0.0)) return 0;
+    if (!(in_view(g, F, dc2) ||
+          (rule == 1 && (in_view(s->a[t], F, dc2) || in_view(s->b[t], F, dc2) || in_view(s->c[t], F, dc2)))))
+        return 0;
     d3 cl = ld3(L->center);
     if (!(dot(cr, sub(cl, g)) > 0.0)) return 0;
     if (L->type == 0 && !(dot(ld3(L->normal), sub(g, cl)) > 0.0)) return 0;
     return 1;
 }
 
-ORC_API int64_t orc_classify(void *sp, const ocamera *cam, const olight *L, double d_close,
+ORC_API int64_t orc_classify(void *sp, const ocamera *cam, const olight *L, double d_close, int32_t rule,
                              uint8_t *flags)
 {
     const oscene *s = (const oscene *)sp;
@@ -514,7 +526,7 @@ ORC_API int64_t orc_classify(void *sp, const ocamera *cam, const olight *L, doub
     double dc2 = d_close * d_close;
     int64_t n = 0;
     for (int64_t t = 0; t < s->nt; t++) {
-        flags[t] = (uint8_t)is_close(s, t, &F, L, dc2);
+        flags[t] = (uint8_t)is_close(s, t, &F, L, dc2, rule);
         n += flags[t];
     }
     return n;
@@ -653,7 +665,7 @@ ORC_API int64_t orc_generate(void *sp, const ocamera *cam, const olight *L, cons
 
     /* (1) close-range faces */
     uint8_t *close = calloc((size_t)(s->nt > 0 ? s->nt : 1), 1);
-    int64_t nc = orc_classify(sp, cam, L, G->d_close, close);
+    int64_t nc = orc_classify(sp, cam, L, G->d_close, G->close_rule, close);
     info->n_close = nc;
 
     /* (2) patch sampling of the close range */

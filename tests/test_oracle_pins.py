@@ -128,6 +128,34 @@ def test_classify_hand_cases(orc):
     assert orc.OracleScene(sc3).classify(_cam(), 3.0).tolist() == [False]
 
 
+def test_classify_any_vertex_rule(orc):
+    """Rule 1 also accepts a face whose centroid fails the view or distance
+    test when one of its vertices passes it (camera at the origin looking
+    down +z, vfov 60 deg: the view edge at z = 1 is |x| = tan 30 deg = 0.577)."""
+    light = W.Light(center=(0.0, 0.0, -1.0), normal=(0.0, 0.0, 1.0), edge_u=(0.1, 0, 0),
+                    edge_v=(0, 0.1, 0), type=W.LIGHT_POINT)
+    def facing(a, b, c):          # front side towards the camera (normal -z)
+        return [a, c, b]
+    tris_v = [
+        facing((0.5, 0, 1), (0.9, 0, 1), (0.9, 0.3, 1)),   # 0 centroid x 0.77 outside, vertex x 0.5 inside
+        facing((0, 0, 2.9), (0.1, 0, 3.5), (0, 0.1, 3.5)),  # 1 centroid at z 3.3 > d_close 3, a vertex at 2.9
+        facing((0, 0, 1), (0.1, 0, 1), (0, 0.1, 1)),        # 2 centroid inside: close under both rules
+        facing((1.0, 0, 1), (1.2, 0, 1), (1.2, 0.2, 1)),    # 3 all outside: close under neither
+        [(0.5, 0, 1), (0.9, 0, 1), (0.9, 0.3, 1)],           # 4 as 0 but its back towards the camera
+    ]
+    verts = np.array([p for t in tris_v for p in t], np.float32)
+    tris = np.arange(len(verts)).reshape(-1, 3)
+    o = orc.OracleScene(tri_scene(verts, tris, 0.5, light))
+    assert o.classify(_cam(), 3.0, rule=0).tolist() == [False, False, True, False, False]
+    assert o.classify(_cam(), 3.0, rule=1).tolist() == [True, True, True, False, False]
+    # on a whole scene the any-vertex set contains the centroid set
+    wl = W.cornell_workload()
+    oc = orc.OracleScene(wl.scene)
+    c0 = oc.classify(wl.views[0].camera, wl.views[0].gen.d_close, rule=0)
+    c1 = oc.classify(wl.views[0].camera, wl.views[0].gen.d_close, rule=1)
+    assert (c1 | c0).tolist() == c1.tolist() and c1.sum() > c0.sum()
+
+
 def test_cornell_close_fraction(orc):
     wl = W.cornell_workload()
     o = orc.OracleScene(wl.scene)
