@@ -105,6 +105,10 @@ typedef struct {
 
 /* VPL generation (Sec. 3, pipeline steps (1)-(3)).
  *  d_close       close-range distance threshold (camera to face centroid)
+ *  close_rule    where a face is tested for "inside the field of view and
+ *                nearer than d_close": 0 its centroid, 1 its centroid or any
+ *                of its vertices (the paper says only "within the camera's
+ *                field of view"; both readings decide in FP64, exactly)
  *  ray_eps       offset along normals of secondary-ray origins (scene units)
  *  m_close       patch VPLs on the close range (the paper's K)
  *  m_far         instant-radiosity VPLs on the distant part
@@ -116,7 +120,7 @@ typedef struct {
     double d_close;
     float ray_eps;
     int32_t m_close, m_far, max_bounces, light_samples;
-    int32_t reserved;
+    int32_t close_rule;
     int64_t ir_max_paths;
     uint64_t seed;
 } vpl_gen_params;

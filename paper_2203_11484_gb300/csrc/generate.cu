@@ -18,17 +18,27 @@ namespace vpl {
 
 constexpr int kGenThreads = 128;
 
-__device__ __forceinline__ bool is_close(const TriD &T, const GenArgs &g)
+// point p inside the field of view and nearer than d_close
+__device__ __forceinline__ bool in_view(const D3 &p, const GenArgs &g)
 {
     D3 e = dmk(g.eye[0], g.eye[1], g.eye[2]);
     D3 f = dmk(g.f[0], g.f[1], g.f[2]), r = dmk(g.r[0], g.r[1], g.r[2]), u = dmk(g.u[0], g.u[1], g.u[2]);
-    if (!(ddot(T.cr, dsub(e, T.g)) > 0.0)) return false;          // faces the camera
-    D3 v = dsub(T.g, e);
+    D3 v = dsub(p, e);
     double z = ddot(v, f);
     if (!(z > 0.0)) return false;                                  // in front
     if (!(fabs(ddot(v, r)) <= __dmul_rn(z, g.th))) return false;   // horizontal field of view
     if (!(fabs(ddot(v, u)) <= __dmul_rn(z, g.tv))) return false;   // vertical field of view
-    if (!(ddot(v, v) < __dmul_rn(g.d_close, g.d_close))) return false; // nearer than d_close
+    return ddot(v, v) < __dmul_rn(g.d_close, g.d_close);           // nearer than d_close
+}
+
+// close range: faces the camera, in view and range at its centroid (rule 0)
+// or at its centroid or any vertex (rule 1), and faces the light
+__device__ __forceinline__ bool is_close(const TriD &T, const GenArgs &g)
+{
+    D3 e = dmk(g.eye[0], g.eye[1], g.eye[2]);
+    if (!(ddot(T.cr, dsub(e, T.g)) > 0.0)) return false;          // faces the camera
+    if (!(in_view(T.g, g) || (g.close_rule == 1 && (in_view(T.a, g) || in_view(T.b, g) || in_view(T.c, g)))))
+        return false;
     D3 cl = dld(g.light.center);
     if (!(ddot(T.cr, dsub(cl, T.g)) > 0.0)) return false;          // faces the light
     if (g.light.type == VPL_LIGHT_AREA && !(ddot(dld(g.light.normal), dsub(T.g, cl)) > 0.0)) return false;

@@ -102,7 +102,7 @@ __device__ __forceinline__ D3 dvert(const float *v, int32_t i)
 __device__ __forceinline__ D3 dld(const float *p) { return dmk((double)p[0], (double)p[1], (double)p[2]); }
 
 // triangle quantities used by decisions (same operation order as the FP64 reference)
-struct TriD { D3 a, e1, e2, cr, g; double area; };
+struct TriD { D3 a, b, c, e1, e2, cr, g; double area; };
 __device__ __forceinline__ TriD tri_exact(const SceneView &s, int32_t t)
 {
     TriD r;
@@ -110,6 +110,8 @@ __device__ __forceinline__ TriD tri_exact(const SceneView &s, int32_t t)
     D3 b = dvert(s.verts, s.idx[3 * (int64_t)t + 1]);
     D3 c = dvert(s.verts, s.idx[3 * (int64_t)t + 2]);
     r.a = a;
+    r.b = b;
+    r.c = c;
     r.e1 = dsub(b, a);
     r.e2 = dsub(c, a);
     r.cr = dcross(r.e1, r.e2);

@@ -9,6 +9,8 @@ same seeded inputs (Jin et al., arXiv 2203.11484, Sec. 3 and Eqs. 1-2).
 """
 import math
 
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -188,11 +190,13 @@ def _light_flip_ok(osc, wl, gen, k, x, n):
     return osc.segment_margin(xo, y) <= PY.FLIP_MARGIN * wl.scene.diag()
 
 
+@pytest.mark.parametrize("rule", [0, 1])
 @pytest.mark.parametrize("which", ["cornell", "room"])
-def test_generate_parity(V, ctx, which, request):
+def test_generate_parity(V, ctx, which, rule, request):
+    """Both close-range rules (centroid; centroid or any vertex)."""
     wl, sid, osc = request.getfixturevalue(which)
     view = wl.views[0]
-    cam, gen = view.camera, view.gen
+    cam, gen = view.camera, dataclasses.replace(view.gen, close_rule=rule)
     g, _ = _generate(V, ctx, sid, cam, gen)
     r = osc.generate(cam, gen, vis_mode=0)
     assert g["status"] == 0 and r["status"] == 0
