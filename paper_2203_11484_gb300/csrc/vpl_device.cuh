@@ -179,7 +179,7 @@ struct Ray {
 __device__ __forceinline__ float safe_inv(float v)
 {
     const float tiny = 1e-20f;
-    return 1.0f / (fabsf(v) < tiny ? copysignf(tiny, v) : v);
+    return __frcp_rn(fabsf(v) < tiny ? copysignf(tiny, v) : v); // correctly rounded, as 1.0f / v
 }
 
 __device__ __forceinline__ Ray make_ray(float3 o, float3 d)
@@ -208,6 +208,27 @@ __device__ __forceinline__ bool tri_hit(const Ray &r, float4 v0, float4 e1v, flo
     if (v < 0.0f || __fadd_rn(u, v) > 1.0f) return false;
     t = __fmul_rn(dot(e2, qv), inv);
     return true;
+}
+
+// Moller-Trumbore for a shadow segment, without the division: the
+// barycentric and segment bounds are compared against |det| after the signs
+// are made positive (u in [0, |det|], v >= 0, u + v <= |det|, t in
+// (0, |det|) -- the tests of tri_hit scaled by |det|); either side blocks.
+__device__ __forceinline__ bool seg_block(const Ray &r, float4 v0, float4 e1v, float4 e2v)
+{
+    const float3 e1 = f3(e1v), e2 = f3(e2v);
+    const float3 pv = cross(r.d, e2);
+    const float det = dot(e1, pv);
+    if (det == 0.0f) return false;
+    const float sg = det < 0.0f ? -1.0f : 1.0f, ad = fabsf(det);
+    const float3 tv = r.o - f3(v0);
+    const float u = __fmul_rn(dot(tv, pv), sg);
+    if (u < 0.0f || u > ad) return false;
+    const float3 qv = cross(tv, e1);
+    const float v = __fmul_rn(dot(r.d, qv), sg);
+    if (v < 0.0f || __fadd_rn(u, v) > ad) return false;
+    const float t = __fmul_rn(dot(e2, qv), sg);
+    return t > 0.0f && t < ad;
 }
 
 // --------------------------------------------------------------------------
@@ -396,12 +417,9 @@ static __device__ __noinline__ bool occluded1(const SceneView &s, const Ray &r, 
             int rf = n.ref[k];
             if (rf == kEmptyRef || !slab(r, n, k, 0.0f, 1.0f, te)) continue;
             if (rf < 0) {
-                for (int q = ~rf; q < ~rf + n.cnt[k]; q++) {
-                    float t;
-                    if (tri_hit(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2), t) &&
-                        t > 0.0f && t < 1.0f)
+                for (int q = ~rf; q < ~rf + n.cnt[k]; q++)
+                    if (seg_block(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2)))
                         return true;
-                }
             } else if (next < 0) {
                 next = rf;
             } else {
@@ -439,12 +457,8 @@ __device__ __forceinline__ int closest_brute(const SceneView &s, const Ray &r, f
 
 __device__ __forceinline__ bool occluded_brute(const SceneView &s, const Ray &r)
 {
-    for (int k = 0; k < s.n_tris; k++) {
-        float t;
-        if (tri_hit(r, __ldg(s.tri + 3 * k), __ldg(s.tri + 3 * k + 1), __ldg(s.tri + 3 * k + 2), t) &&
-            t > 0.0f && t < 1.0f)
-            return true;
-    }
+    for (int k = 0; k < s.n_tris; k++)
+        if (seg_block(r, __ldg(s.tri + 3 * k), __ldg(s.tri + 3 * k + 1), __ldg(s.tri + 3 * k + 2))) return true;
     return false;
 }
 
@@ -478,17 +492,13 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     const int lane = threadIdx.x & 31;
     bool occl = false;
     if (want && cache >= 0) {
-        float t;
         if (COUNT) wc.tests++;
-        if (tri_hit(r, __ldg(s.tri + 3 * cache), __ldg(s.tri + 3 * cache + 1), __ldg(s.tri + 3 * cache + 2), t) &&
-            t > 0.0f && t < 1.0f)
+        if (seg_block(r, __ldg(s.tri + 3 * cache), __ldg(s.tri + 3 * cache + 1), __ldg(s.tri + 3 * cache + 2)))
             occl = true;
     }
     if (want && !occl && cache2 >= 0) {
-        float t;
         if (COUNT) wc.tests++;
-        if (tri_hit(r, __ldg(s.tri + 3 * cache2), __ldg(s.tri + 3 * cache2 + 1), __ldg(s.tri + 3 * cache2 + 2), t) &&
-            t > 0.0f && t < 1.0f) {
+        if (seg_block(r, __ldg(s.tri + 3 * cache2), __ldg(s.tri + 3 * cache2 + 1), __ldg(s.tri + 3 * cache2 + 2))) {
             occl = true;
             const int x = cache; cache = cache2; cache2 = x;
         }
@@ -552,10 +562,8 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
                     const int k = __ffs(todo) - 1;
                     todo &= todo - 1;
                     const int q = n.lbase + __popc(leafmask & ((1u << k) - 1u));
-                    float t;
                     if (COUNT) wc.tests++;
-                    if (tri_hit(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2), t) &&
-                        t > 0.0f && t < 1.0f) {
+                    if (seg_block(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2))) {
                         occl = true;
                         cache2 = cache;
                         cache = q;
@@ -598,9 +606,8 @@ __device__ __forceinline__ bool warp_occluded_brute(const SceneView &s, bool wan
         if (COUNT) wc.steps++;
         float4 v0 = __ldg(s.tri + 3 * k), e1 = __ldg(s.tri + 3 * k + 1), e2 = __ldg(s.tri + 3 * k + 2);
         if (want && !occl) {
-            float t;
             if (COUNT) wc.tests++;
-            if (tri_hit(r, v0, e1, e2, t) && t > 0.0f && t < 1.0f) occl = true;
+            if (seg_block(r, v0, e1, e2)) occl = true;
         }
     }
     return occl;
