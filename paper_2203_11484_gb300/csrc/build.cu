@@ -799,6 +799,37 @@ __global__ void collapse_init_kernel(int2 *queue, int *count, int *next)
     next[1] = 0;  // triangle slots handed out
 }
 
+#ifndef VPL_LEAF_MAX
+#define VPL_LEAF_MAX 2
+#endif
+constexpr int kLeafMax = VPL_LEAF_MAX; // triangles per leaf slot
+static_assert(kLeafMax >= 1 && kLeafMax <= 4, "a node's leaf runs are addressed with 4-bit offsets");
+
+// Leaves of the binary subtree under c in depth-first order, if there are at
+// most kLeafMax of them (c < 0: the one leaf ~c); else -1.
+__device__ __forceinline__ int small_subtree(const int *child, int c, int *tris)
+{
+    if (c < 0) {
+        tris[0] = ~c;
+        return 1;
+    }
+    if (kLeafMax < 2) return -1;
+    int stack[kLeafMax + 1], sp = 0, n = 0;
+    stack[sp++] = c;
+    while (sp > 0) {
+        const int x = stack[--sp];
+        if (x < 0) {
+            if (n == kLeafMax) return -1;
+            tris[n++] = ~x;
+            continue;
+        }
+        if (sp + 2 > kLeafMax + 1) return -1; // more than kLeafMax leaves below
+        stack[sp++] = child[2 * x + 1];
+        stack[sp++] = child[2 * x];
+    }
+    return n;
+}
+
 template <bool EVEN>
 __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, int *count, int *next,
                                       const int *child, const float *leafbox, const float *nodebox, float4 *nodes,
@@ -808,20 +839,27 @@ __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, in
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_in; q += gridDim.x * blockDim.x) {
         const int2 w = qin[q];
         int slot[4] = {child[2 * w.x], child[2 * w.x + 1], 0, 0};
+        int tris[kLeafMax];
+        // a slot is a leaf when its subtree has at most kLeafMax triangles
+        bool leaf[4] = {small_subtree(child, slot[0], tris) > 0, small_subtree(child, slot[1], tris) > 0, false,
+                        false};
         int m = 2;
         if (EVEN) {
             for (int k = 0; k < 2; k++)
-                if (slot[k] >= 0) {
+                if (!leaf[k]) {
                     const int c = slot[k];
                     slot[k] = child[2 * c];
-                    slot[m++] = child[2 * c + 1];
+                    slot[m] = child[2 * c + 1];
+                    leaf[k] = small_subtree(child, slot[k], tris) > 0;
+                    leaf[m] = small_subtree(child, slot[m], tris) > 0;
+                    m++;
                 }
         } else {
             while (m < 4) {
                 int pick = -1;
                 float best = -1.0f;
                 for (int k = 0; k < m; k++)
-                    if (slot[k] >= 0) {
+                    if (!leaf[k]) {
                         const float a = box_area(nodebox + 6 * (int64_t)slot[k]);
                         if (pick < 0 || a > best) {
                             pick = k;
@@ -831,7 +869,10 @@ __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, in
                 if (pick < 0) break;
                 const int c = slot[pick];
                 slot[pick] = child[2 * c];
-                slot[m++] = child[2 * c + 1];
+                slot[m] = child[2 * c + 1];
+                leaf[pick] = small_subtree(child, slot[pick], tris) > 0;
+                leaf[m] = small_subtree(child, slot[m], tris) > 0;
+                m++;
             }
         }
         // slot order: box surface, largest first (stable)
@@ -842,25 +883,28 @@ __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, in
             for (int j = i; j > 0 && area[j] > area[j - 1]; j--) {
                 float ta = area[j]; area[j] = area[j - 1]; area[j - 1] = ta;
                 int ts = slot[j]; slot[j] = slot[j - 1]; slot[j - 1] = ts;
+                bool tl = leaf[j]; leaf[j] = leaf[j - 1]; leaf[j - 1] = tl;
             }
-        int n_int = 0, n_leaf = 0;
+        int n_int = 0, n_tri = 0;
         for (int k = 0; k < m; k++) {
-            n_int += slot[k] >= 0;
-            n_leaf += slot[k] < 0;
+            if (leaf[k]) n_tri += small_subtree(child, slot[k], tris);
+            else n_int++;
         }
         const int ibase = n_int ? atomicAdd(&next[0], n_int) : 0;
-        const int lbase = n_leaf ? atomicAdd(&next[1], n_leaf) : 0;
+        const int lbase = n_tri ? atomicAdd(&next[1], n_tri) : 0;
         const int pos = n_int ? atomicAdd(&count[(level + 1) & 1], n_int) : 0;
         // empty slots: a point box at (3e38, -3e38, 3e38), which no segment or
         // ray of a scene reaches
         float lo[3][4], hi[3][4];
-        unsigned leafmask = 0, intmask = 0;
+        unsigned leafmask = 0, intmask = 0, runs = 0;
         int ji = 0, jl = 0;
         for (int k = 0; k < 4; k++) {
             const float *b = nullptr;
-            if (k < m && slot[k] < 0) {
-                b = leafbox + 6 * (int64_t)(~slot[k]);
-                leaf_src[lbase + jl++] = ~slot[k];
+            if (k < m && leaf[k]) {
+                b = slot[k] < 0 ? leafbox + 6 * (int64_t)(~slot[k]) : nodebox + 6 * (int64_t)slot[k];
+                const int n = small_subtree(child, slot[k], tris);
+                runs |= (unsigned)(jl | (n << 4)) << (8 * k); // offset in the node's run, count
+                for (int i = 0; i < n; i++) leaf_src[lbase + jl++] = tris[i];
                 leafmask |= 1u << k;
             } else if (k < m) {
                 b = nodebox + 6 * (int64_t)slot[k];
@@ -881,7 +925,7 @@ __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, in
         o[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
         o[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
         o[6] = make_float4(__int_as_float(ibase), __int_as_float(lbase), __uint_as_float(leafmask | (intmask << 4)),
-                           0.0f);
+                           __uint_as_float(runs));
         o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
@@ -951,7 +995,7 @@ __global__ void single_root_kernel(const float *leafbox, float4 *nodes)
     nodes[3] = make_float4(a[4], -f, -f, -f);
     nodes[4] = make_float4(a[2], f, f, f);
     nodes[5] = make_float4(a[5], f, f, f);
-    nodes[6] = make_float4(__int_as_float(0), __int_as_float(0), __uint_as_float(1u), 0.0f);
+    nodes[6] = make_float4(__int_as_float(0), __int_as_float(0), __uint_as_float(1u), __uint_as_float(1u << 4));
     nodes[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 

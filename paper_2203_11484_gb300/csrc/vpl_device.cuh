@@ -233,11 +233,12 @@ __device__ __forceinline__ bool seg_block(const Ray &r, float4 v0, float4 e1v, f
 
 // --------------------------------------------------------------------------
 // 4-wide BVH nodes (8 float4 = 128 B): rows 0-5 lo.x / hi.x / lo.y / hi.y /
-// lo.z / hi.z of the four child slots; row 6 (ibase, lbase, masks, 0) with
-// masks bits 0-3 = leaf slots, bits 4-7 = internal slots; row 7 unused.  A
-// node's internal children are nodes ibase, ibase + 1, ... and its leaves
-// (one triangle each) triangle slots lbase, lbase + 1, ..., both in slot
-// order; an empty slot holds a box no segment reaches.
+// lo.z / hi.z of the four child slots; row 6 (ibase, lbase, masks, runs)
+// with masks bits 0-3 = leaf slots, bits 4-7 = internal slots; row 7 unused.
+// A node's internal children are nodes ibase, ibase + 1, ... in slot order;
+// leaf slot k holds the triangle slots lbase + off_k ... + cnt_k - 1 (byte k
+// of runs: off_k in bits 0-3, cnt_k in bits 4-6); an empty slot holds a box
+// no segment reaches.
 // --------------------------------------------------------------------------
 constexpr int kEmptyRef = (int)0x80000000;
 
@@ -245,6 +246,7 @@ struct Node4 {
     float4 lx, hx, ly, hy, lz, hz;
     int ibase, lbase;           // first internal child node / first leaf triangle slot
     unsigned leafmask, intmask; // bit k: slot k holds a leaf / an internal node
+    unsigned runs;              // byte k: leaf slot k's offset from lbase (bits 0-3), triangles (4-6)
     int ref[4], cnt[4];         // decoded per slot (load_node4 only)
 };
 
@@ -257,6 +259,7 @@ __device__ __forceinline__ void load_node4_meta(const float4 *p, Node4 &n)
     const unsigned m = __float_as_uint(r.z);
     n.leafmask = m & 15u;
     n.intmask = (m >> 4) & 15u;
+    n.runs = __float_as_uint(r.w);
 }
 
 // whole node, with each slot's reference decoded: >= 0 internal node,
@@ -275,8 +278,8 @@ __device__ __forceinline__ void load_node4(const float4 *nodes, int node, Node4 
     for (int k = 0; k < 4; k++) {
         const unsigned below = (1u << k) - 1u;
         if ((n.leafmask >> k) & 1u) {
-            n.ref[k] = ~(n.lbase + __popc(n.leafmask & below));
-            n.cnt[k] = 1;
+            n.ref[k] = ~(n.lbase + (int)((n.runs >> (8 * k)) & 15u));
+            n.cnt[k] = (int)((n.runs >> (8 * k + 4)) & 7u);
         } else if ((n.intmask >> k) & 1u) {
             n.ref[k] = n.ibase + __popc(n.intmask & below);
             n.cnt[k] = 0;
@@ -561,12 +564,15 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
                 if (todo != 0 && !occl) {
                     const int k = __ffs(todo) - 1;
                     todo &= todo - 1;
-                    const int q = n.lbase + __popc(leafmask & ((1u << k) - 1u));
-                    if (COUNT) wc.tests++;
-                    if (seg_block(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2))) {
-                        occl = true;
-                        cache2 = cache;
-                        cache = q;
+                    const unsigned run = n.runs >> (8 * k);
+                    const int q0 = n.lbase + (int)(run & 15u), q1 = q0 + (int)((run >> 4) & 7u);
+                    for (int q = q0; q < q1 && !occl; q++) {
+                        if (COUNT) wc.tests++;
+                        if (seg_block(r, __ldg(s.tri + 3 * q), __ldg(s.tri + 3 * q + 1), __ldg(s.tri + 3 * q + 2))) {
+                            occl = true;
+                            cache2 = cache;
+                            cache = q;
+                        }
                     }
                 }
             }
