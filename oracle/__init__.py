@@ -55,7 +55,7 @@ class _Gen(C.Structure):
     _fields_ = [("d_close", C.c_double), ("ray_eps", C.c_double), ("ir_max_paths", C.c_int64),
                 ("seed", C.c_uint64), ("m_close", C.c_int32), ("m_far", C.c_int32),
                 ("max_bounces", C.c_int32), ("light_samples", C.c_int32),
-                ("vis_mode", C.c_int32), ("close_rule", C.c_int32)]
+                ("vis_mode", C.c_int32), ("close_rule", C.c_int32), ("patch_rule", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -160,6 +160,7 @@ def gen_struct(gen, vis_mode: int) -> _Gen:
     g.max_bounces, g.light_samples = int(gen.max_bounces), int(gen.light_samples)
     g.vis_mode = int(vis_mode)
     g.close_rule = int(getattr(gen, "close_rule", 0))
+    g.patch_rule = int(getattr(gen, "patch_rule", 0))
     return g
 
 

@@ -164,6 +164,7 @@ typedef struct {
     int32_t m_close, m_far, max_bounces, light_samples;
     int32_t vis_mode;      /* 0 BVH, 1 brute force */
     int32_t close_rule;    /* 0 centroid, 1 centroid or any vertex (see is_close) */
+    int32_t patch_rule;    /* 0 a point per stratum, 1 set sum for strata over several faces */
 } ogen;
 
 /* ---- FP64 BVH: top-down median split, boxes padded so that the set of
@@ -717,6 +718,46 @@ ORC_API int64_t orc_generate(void *sp, const ocamera *cam, const olight *L, cons
                     if (f[mid] <= u) lo = mid; else hi = mid;
                 }
                 int64_t t = keys[lo].tri;
+                if (G->patch_rule == 1) {
+                    /* the faces overlapping the stratum [A, B) of the prefix */
+                    uint64_t A = (uint64_t)(((unsigned __int128)k * F) / K);
+                    uint64_t B = (uint64_t)(((unsigned __int128)(k + 1) * F) / K);
+                    int64_t m0 = lo, m1 = lo;
+                    while (m0 > 0 && f[m0] > A) m0--;              /* f[m0] <= A < f[m0 + 1] */
+                    while (m1 + 1 < nc && f[m1 + 1] < B) m1++;     /* f[m1] < B <= f[m1 + 1] */
+                    if (m1 > m0) {
+                        /* set sum: each face's Eq. 2 at its centroid with the
+                         * area it gives to the stratum; the VPL at the
+                         * area-weighted centroid, normal the area-weighted
+                         * normal, face the one giving the most area */
+                        d3 fl = mk(0, 0, 0), xs = mk(0, 0, 0), ns = mk(0, 0, 0);
+                        double Dsum = 0.0;
+                        uint64_t wbest = 0;
+                        int64_t tbest = keys[m0].tri;
+                        for (int64_t m = m0; m <= m1; m++) {
+                            uint64_t lo_m = f[m] > A ? f[m] : A, hi_m = f[m + 1] < B ? f[m + 1] : B;
+                            if (hi_m <= lo_m) continue;
+                            uint64_t wm = hi_m - lo_m;
+                            int64_t tm = keys[m].tri;
+                            double Dm = ldexp((double)wm, -S);
+                            fl = add(fl, patch_flux(s, L, G, (int64_t)k, s->g[tm], s->n[tm], s->rho + 3 * tm, Dm));
+                            xs = add(xs, scl(s->g[tm], Dm));
+                            ns = add(ns, scl(s->n[tm], Dm));
+                            Dsum += Dm;
+                            if (wm > wbest) {
+                                wbest = wm;
+                                tbest = tm;
+                            }
+                        }
+                        double nl = len(ns);
+                        st3(pos + 3 * k, scl(xs, 1.0 / Dsum));
+                        st3(nrm + 3 * k, nl > 0.0 ? scl(ns, 1.0 / nl) : s->n[tbest]);
+                        st3(flux + 3 * k, fl);
+                        tri[k] = tbest;
+                        tag[k] = (int64_t)k;
+                        continue;
+                    }
+                }
                 /* uniform random point in triangle t */
                 double r1 = u01(w[1]), r2 = u01(w[2]);
                 double sr = sqrt(r1);

@@ -68,6 +68,7 @@ class GenParams:
     ir_max_paths: int = 0        # 0 -> default 16*m_far + 4096
     ray_eps: float = 1e-5
     close_rule: int = 0          # 0 centroid, 1 centroid or any vertex in view and range
+    patch_rule: int = 0          # 0 a point per stratum, 1 set sum when a stratum spans several faces
 
     def resolved_max_paths(self) -> int:
         return self.ir_max_paths if self.ir_max_paths > 0 else 16 * self.m_far + 4096

@@ -593,3 +593,64 @@ def test_direct_term_matches_lambert(orc):
     away = dict(pos=np.array([[0.1, 0.2, 0.0], [0.1, 0.2, 2.0]]), nrm=np.array([[0, 0, -1.0], [0, 0, 1.0]]),
                 rho=np.full((2, 3), 0.6), tri=np.zeros(2, np.int64))
     assert np.array_equal(o.gather(away, v, d2_min=1e-12, eps=1e-9, vis_mode=1), np.zeros((2, 3)))
+
+
+# ---------------------------------------------------------------------------
+# patch rule 1 (set sum): a stratum over several faces is one VPL whose value
+# is the sum of the faces' Eq. 2 terms with the areas they give it
+# ---------------------------------------------------------------------------
+def _grid_scene(n, half, light, albedo=0.5):
+    xs = np.linspace(-half, half, n + 1)
+    verts = np.array([(x, y, 0.0) for y in xs for x in xs], np.float32)
+    tris = []
+    for j in range(n):
+        for i in range(n):
+            a, b = j * (n + 1) + i, j * (n + 1) + i + 1
+            c, d = a + n + 1, b + n + 1
+            tris += [(a, b, d), (a, d, c)]
+    return tri_scene(verts, tris, albedo, light)
+
+
+def test_set_sum_total_flux_and_placement(orc):
+    """With faces much smaller than a stratum every VPL sums several faces:
+    the total flux is exactly sum_t rho E(c_t) A_t (E of the point light at
+    each face's centroid; the quantised areas split without loss), each VPL
+    lies at the area-weighted centroid of its faces, on the plane, inside
+    the grid, with the plane's normal."""
+    light = W.Light(center=(0.3, -0.2, 2.0), normal=(0, 0, -1), edge_u=(1, 0, 0), edge_v=(0, 1, 0),
+                    power=(1.0, 2.0, 0.5), type=W.LIGHT_POINT)
+    sc = _grid_scene(40, 1.5, light, albedo=0.5)
+    cam = _cam(eye=(0, 0, 4), fwd=(0, 0, -1), up=(0, 1, 0), vfov=80)
+    o = orc.OracleScene(sc)
+    K = 50
+    g = o.generate(cam, W.GenParams(d_close=100.0, m_close=K, m_far=0, seed=3, patch_rule=1))
+    assert g["status"] == 0 and g["n_close"] == 3200
+    V = sc.verts.astype(np.float64)
+    T = sc.tris
+    cen = V[T].mean(axis=1)
+    area = 0.5 * np.linalg.norm(np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]]), axis=1)
+    p = np.array(light.center, np.float64)
+    dv = p - cen
+    r = np.linalg.norm(dv, axis=1)
+    E = np.maximum(dv[:, 2] / r, 0) / (4 * math.pi * r * r)
+    want = 0.5 * np.array(light.power) * (E * area).sum()
+    assert np.allclose(g["flux"].sum(axis=0), want, rtol=1e-9)
+    assert np.allclose(g["pos"][:, 2], 0.0, atol=1e-12)
+    assert (np.abs(g["pos"][:, :2]) <= 1.5).all()
+    assert np.allclose(g["nrm"], [0, 0, 1.0])
+    # consecutive strata cover consecutive runs of faces: their VPLs differ
+    assert len({tuple(np.round(x, 9)) for x in g["pos"]}) == K
+
+
+def test_set_sum_equals_point_rule_inside_single_faces(orc):
+    """A stratum inside one face keeps the point rule: on two large faces
+    only the stratum that straddles their common edge can differ."""
+    light = W.Light(center=(0.3, -0.2, 2.0), normal=(0, 0, -1), edge_u=(1, 0, 0), edge_v=(0, 1, 0),
+                    power=(1.0, 2.0, 0.5), type=W.LIGHT_POINT)
+    sc = plane_scene(half=1.5, albedo=0.5, light=light)
+    cam = _cam(eye=(0, 0, 4), fwd=(0, 0, -1), up=(0, 1, 0), vfov=80)
+    o = orc.OracleScene(sc)
+    a = o.generate(cam, W.GenParams(d_close=100.0, m_close=64, m_far=0, seed=9, patch_rule=0))
+    b = o.generate(cam, W.GenParams(d_close=100.0, m_close=64, m_far=0, seed=9, patch_rule=1))
+    same = (a["pos"] == b["pos"]).all(axis=1) & (a["flux"] == b["flux"]).all(axis=1)
+    assert same.sum() >= 63 and np.array_equal(a["tri"][same], b["tri"][same])
