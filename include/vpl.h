@@ -80,6 +80,7 @@ typedef enum {
 } vpl_status;
 
 enum { VPL_LIGHT_AREA = 0, VPL_LIGHT_POINT = 1 };
+enum { VPL_RULE_ANY_VERTEX = 1, VPL_RULE_SET_SUM = 2 };
 enum { VPL_PREC_FP32 = 0, VPL_PREC_FP16_KAHAN = 1, VPL_PREC_FP16_PLAIN = 2 };
 enum { VPL_VIS_BVH = 0, VPL_VIS_BRUTE = 1, VPL_VIS_NONE = 2 };
 enum { VPL_FORMAT_FP32 = 0, VPL_FORMAT_FP16 = 1 };
@@ -105,10 +106,16 @@ typedef struct {
 
 /* VPL generation (Sec. 3, pipeline steps (1)-(3)).
  *  d_close       close-range distance threshold (camera to face centroid)
- *  close_rule    where a face is tested for "inside the field of view and
- *                nearer than d_close": 0 its centroid, 1 its centroid or any
- *                of its vertices (the paper says only "within the camera's
- *                field of view"; both readings decide in FP64, exactly)
+ *  rules         readings of the paper, as bits (0 = the defaults):
+ *                VPL_RULE_ANY_VERTEX: a face is "inside the field of view
+ *                and nearer than d_close" at its centroid or any vertex (else
+ *                at its centroid; both decide in FP64, exactly);
+ *                VPL_RULE_SET_SUM: a stratum that spans several close faces
+ *                gives one VPL at their area-weighted centroid with the sum
+ *                of their Eq. 2 terms, each at the face's centroid with the
+ *                area it gives the stratum, tagged with the face giving the
+ *                most area (else a random point of the face at the
+ *                stratum's jittered point)
  *  ray_eps       offset along normals of secondary-ray origins (scene units)
  *  m_close       patch VPLs on the close range (the paper's K)
  *  m_far         instant-radiosity VPLs on the distant part
@@ -120,7 +127,7 @@ typedef struct {
     double d_close;
     float ray_eps;
     int32_t m_close, m_far, max_bounces, light_samples;
-    int32_t close_rule;
+    int32_t rules;
     int64_t ir_max_paths;
     uint64_t seed;
 } vpl_gen_params;

@@ -244,7 +244,7 @@ int check_gen(vpl_ctx *ctx, const vpl_gen_params *g)
     if (g->m_close < 0 || g->m_far < 0) return fail(ctx, VPL_ERR_INVALID_ARG, "m_close / m_far must be >= 0");
     if (g->max_bounces < 1 || g->max_bounces > 15) return fail(ctx, VPL_ERR_INVALID_ARG, "max_bounces must be 1..15");
     if (g->light_samples < 1) return fail(ctx, VPL_ERR_INVALID_ARG, "light_samples must be >= 1");
-    if (g->close_rule != 0 && g->close_rule != 1) return fail(ctx, VPL_ERR_INVALID_ARG, "close_rule must be 0 or 1");
+    if (g->rules & ~(VPL_RULE_ANY_VERTEX | VPL_RULE_SET_SUM)) return fail(ctx, VPL_ERR_INVALID_ARG, "unknown rule bits");
     if (!(g->d_close >= 0.0) || !std::isfinite(g->d_close)) return fail(ctx, VPL_ERR_INVALID_ARG, "d_close must be >= 0");
     if (!(g->ray_eps >= 0.0f) || !std::isfinite(g->ray_eps)) return fail(ctx, VPL_ERR_INVALID_ARG, "ray_eps must be >= 0");
     if (g->ir_max_paths < 0 || g->ir_max_paths > ((int64_t)1 << 26))
@@ -262,7 +262,8 @@ GenArgs gen_args(const Frame &F, const vpl_gen_params *g, const vpl_light &L)
     a.m_far = g->m_far;
     a.max_bounces = g->max_bounces;
     a.light_samples = g->light_samples;
-    a.close_rule = g->close_rule;
+    a.close_rule = (g->rules & VPL_RULE_ANY_VERTEX) ? 1 : 0;
+    a.patch_rule = (g->rules & VPL_RULE_SET_SUM) ? 1 : 0;
     a.max_paths = g->ir_max_paths > 0 ? g->ir_max_paths : 16 * (int64_t)g->m_far + 4096;
     a.seed = g->seed;
     for (int k = 0; k < 3; k++) {

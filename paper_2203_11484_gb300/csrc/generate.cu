@@ -168,6 +168,38 @@ __device__ __forceinline__ bool seg_blocked(const SceneView &s, D3 p, D3 q, int 
 }
 
 // (2): one thread per stratum k
+// Eq. 2 for a VPL k at x (unit normal n) representing area D: the light's
+// power reaching D, as a factor of the power (times the albedo it is the
+// reflected flux); point light literally, area light by light_samples points
+__device__ __forceinline__ double eq2_factor(const SceneView &s, const GenArgs &g, int k, D3 x, D3 n, double D,
+                                            int *status)
+{
+    const LightView &L = g.light;
+    D3 cl = dld(L.center);
+    D3 xo = dadd(x, dscl(n, (double)g.ray_eps));
+    double acc = 0.0;
+    if (L.type == VPL_LIGHT_POINT) {
+        D3 dv = dsub(cl, x);
+        double r = sqrt(ddot(dv, dv));
+        double cw = ddot(n, dv) / r;
+        if (cw > 0.0 && !seg_blocked(s, xo, cl, status)) acc = D * cw / (4.0 * kPiD * r * r);
+    } else {
+        D3 nL = dld(L.normal);
+        for (int j = 0; j < g.light_samples; j++) {
+            uint64_t v[4];
+            rng4(g.seed, kStreamLight, (uint64_t)k, (uint64_t)j, v);
+            D3 y = light_point(L, u01(v[0]), u01(v[1]));
+            D3 dv = dsub(y, x);
+            double r2s = ddot(dv, dv), r = sqrt(r2s);
+            double cw = ddot(n, dv) / r;
+            double cL = -ddot(nL, dv) / r;
+            if (cw > 0.0 && cL > 0.0 && !seg_blocked(s, xo, y, status)) acc += cw * cL / (kPiD * r2s);
+        }
+        acc = D * acc / (double)g.light_samples;
+    }
+    return acc;
+}
+
 __global__ void patch_kernel(SceneView s, GenArgs g, const uint32_t *sorted, const unsigned long long *F,
                              const int *n_close, const GenInfoDev *info, float4 *pos, void *nrm, void *flux,
                              int fmt, int *status)
@@ -192,6 +224,56 @@ __global__ void patch_kernel(SceneView s, GenArgs g, const uint32_t *sorted, con
         if (F[mid] <= u) lo = mid; else hi = mid;
     }
     const int t = (int)sorted[lo];
+    if (g.patch_rule == 1) {
+        // the faces overlapping the stratum [A, B) of the prefix
+        const uint64_t A = stratum_point((uint64_t)k << 32, Ftot, (uint64_t)g.m_close);
+        const uint64_t B = stratum_point((uint64_t)(k + 1) << 32, Ftot, (uint64_t)g.m_close);
+        int m0 = lo, m1 = lo;
+        while (m0 > 0 && F[m0] > A) m0--;
+        while (m1 + 1 < nc && F[m1 + 1] < B) m1++;
+        if (m1 > m0) {
+            // set sum: each face's Eq. 2 at its centroid with the area it
+            // gives the stratum; the VPL at the area-weighted centroid with
+            // the area-weighted normal, tagged with the face giving most area
+            const int S = (int)info->shift_s;
+            double fl[3] = {0.0, 0.0, 0.0};
+            D3 xs = dmk(0, 0, 0), ns = dmk(0, 0, 0);
+            double Dsum = 0.0;
+            uint64_t wbest = 0;
+            int tbest = (int)sorted[m0];
+            D3 nbest = dmk(0, 0, 0);
+            for (int m = m0; m <= m1; m++) {
+                const uint64_t a = F[m] > A ? F[m] : A, b = F[m + 1] < B ? F[m + 1] : B;
+                if (b <= a) continue;
+                const uint64_t wm = b - a;
+                const int tm = (int)sorted[m];
+                const TriD Tm = tri_exact(s, tm);
+                const double nlm = __dsqrt_rn(ddot(Tm.cr, Tm.cr));
+                const D3 nm = dmk(__ddiv_rn(Tm.cr.x, nlm), __ddiv_rn(Tm.cr.y, nlm), __ddiv_rn(Tm.cr.z, nlm));
+                const double Dm = ldexp((double)wm, -S);
+                const double accm = eq2_factor(s, g, k, Tm.g, nm, Dm, status);
+                const float4 rho = __ldg(s.rho + tm);
+                fl[0] = __dadd_rn(fl[0], __dmul_rn(__dmul_rn((double)rho.x, (double)g.light.power[0]), accm));
+                fl[1] = __dadd_rn(fl[1], __dmul_rn(__dmul_rn((double)rho.y, (double)g.light.power[1]), accm));
+                fl[2] = __dadd_rn(fl[2], __dmul_rn(__dmul_rn((double)rho.z, (double)g.light.power[2]), accm));
+                xs = dadd(xs, dscl(Tm.g, Dm));
+                ns = dadd(ns, dscl(nm, Dm));
+                Dsum = __dadd_rn(Dsum, Dm);
+                if (wm > wbest) {
+                    wbest = wm;
+                    tbest = tm;
+                    nbest = nm;
+                }
+            }
+            const double nl = __dsqrt_rn(ddot(ns, ns));
+            const D3 x = dscl(xs, __ddiv_rn(1.0, Dsum));
+            const D3 n = nl > 0.0 ? dscl(ns, __ddiv_rn(1.0, nl)) : nbest;
+            store_vpl(pos, nrm, flux, k, make_float3((float)x.x, (float)x.y, (float)x.z), tbest,
+                      make_float3((float)n.x, (float)n.y, (float)n.z), k,
+                      make_float3((float)fl[0], (float)fl[1], (float)fl[2]), fmt);
+            return;
+        }
+    }
     TriD T = tri_exact(s, t);
     // uniform point in the triangle (square-root warp)
     double r1 = u01(w[1]), r2 = u01(w[2]);
@@ -203,30 +285,9 @@ __global__ void patch_kernel(SceneView s, GenArgs g, const uint32_t *sorted, con
     D3 n = dmk(__ddiv_rn(T.cr.x, nl), __ddiv_rn(T.cr.y, nl), __ddiv_rn(T.cr.z, nl));
     // Eq. 2 with D = area represented by one VPL
     const double D = ldexp((double)Ftot, -(int)info->shift_s) / (double)g.m_close;
-    const LightView &L = g.light;
-    D3 cl = dld(L.center);
-    D3 xo = dadd(x, dscl(n, (double)g.ray_eps));
-    double acc = 0.0;
-    if (L.type == VPL_LIGHT_POINT) {
-        D3 dv = dsub(cl, x);
-        double r = sqrt(ddot(dv, dv));
-        double cw = ddot(n, dv) / r;
-        if (cw > 0.0 && !seg_blocked(s, xo, cl, status)) acc = D * cw / (4.0 * kPiD * r * r);
-    } else {
-        D3 nL = dld(L.normal);
-        for (int j = 0; j < g.light_samples; j++) {
-            uint64_t v[4];
-            rng4(g.seed, kStreamLight, (uint64_t)k, (uint64_t)j, v);
-            D3 y = light_point(L, u01(v[0]), u01(v[1]));
-            D3 dv = dsub(y, x);
-            double r2s = ddot(dv, dv), r = sqrt(r2s);
-            double cw = ddot(n, dv) / r;
-            double cL = -ddot(nL, dv) / r;
-            if (cw > 0.0 && cL > 0.0 && !seg_blocked(s, xo, y, status)) acc += cw * cL / (kPiD * r2s);
-        }
-        acc = D * acc / (double)g.light_samples;
-    }
+    const double acc = eq2_factor(s, g, k, x, n, D, status);
     float4 rho = __ldg(s.rho + t);
+    const LightView &L = g.light;
     store_vpl(pos, nrm, flux, k, make_float3((float)x.x, (float)x.y, (float)x.z), t,
               make_float3((float)n.x, (float)n.y, (float)n.z), k,
               make_float3((float)((double)rho.x * L.power[0] * acc), (float)((double)rho.y * L.power[1] * acc),

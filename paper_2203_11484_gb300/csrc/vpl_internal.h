@@ -83,6 +83,7 @@ struct GenArgs {
     float ray_eps;
     int32_t m_close, m_far, max_bounces, light_samples;
     int32_t close_rule; // 0 centroid, 1 centroid or any vertex
+    int32_t patch_rule; // 0 a point per stratum, 1 set sum over the stratum's faces
     int64_t max_paths;
     uint64_t seed;
     // camera frame in FP64 (computed on the host)

@@ -45,7 +45,7 @@ class vpl_camera(C.Structure):
 class vpl_gen_params(C.Structure):
     _fields_ = [("d_close", C.c_double), ("ray_eps", C.c_float), ("m_close", C.c_int32),
                 ("m_far", C.c_int32), ("max_bounces", C.c_int32), ("light_samples", C.c_int32),
-                ("close_rule", C.c_int32), ("ir_max_paths", C.c_int64), ("seed", C.c_uint64)]
+                ("rules", C.c_int32), ("ir_max_paths", C.c_int64), ("seed", C.c_uint64)]
 
 
 class vpl_gather_params(C.Structure):
@@ -195,7 +195,7 @@ def make_gen(g: W.GenParams) -> vpl_gen_params:
     s.max_bounces, s.light_samples = int(g.max_bounces), int(g.light_samples)
     s.ir_max_paths = int(g.ir_max_paths)
     s.seed = int(g.seed)
-    s.close_rule = int(g.close_rule)
+    s.rules = (1 if g.close_rule else 0) | (2 if g.patch_rule else 0)
     return s
 
 
