@@ -99,6 +99,9 @@ def lib() -> C.CDLL:
                                      C.c_double, C.c_double, C.c_int32, _D]
             L.orc_pairs.argtypes = [_P, _D, _D, C.c_int64, _D, _D, C.c_double, C.c_double,
                                     C.c_int32, _U8, _D, C.POINTER(C.c_int8), _D]
+            L.orc_generate_rs.argtypes = [_P, C.POINTER(_Cam), C.POINTER(_Light), C.POINTER(_Gen), C.c_int32,
+                                          C.c_double, C.c_double, _D, _D, _D, _I64, _I64, C.POINTER(_Info)]
+            L.orc_generate_rs.restype = C.c_int64
             L.orc_light_vpls.argtypes = [C.POINTER(_Light), C.c_int64, C.c_uint64, _D, _D, _D, _I64]
             L.orc_light_vpls.restype = C.c_int64
             L.orc_num_threads.restype = C.c_int32
@@ -247,6 +250,24 @@ class OracleScene:
                     n_close=info.n_close, shift_s=info.shift_s, f_total=int(info.f_total),
                     paths=info.paths, m_far_kept=info.m_far_kept, a_rep=info.a_rep,
                     status=info.status)
+
+    def generate_rs(self, cam, gen, pilot: int, d2_min: float, eps: float, vis_mode=0) -> dict:
+        """Rejection-sampled instant radiosity (orc_generate_rs): gen.m_far
+        VPLs; `cbar` is the mean candidate contribution on the pilot grid."""
+        M = int(gen.m_far)
+        pos = np.zeros((max(M, 1), 3))
+        nrm = np.zeros((max(M, 1), 3))
+        flux = np.zeros((max(M, 1), 3))
+        tri = np.zeros(max(M, 1), np.int64)
+        tag = np.zeros(max(M, 1), np.int64)
+        info = _Info()
+        c = cam_struct(cam)
+        g = gen_struct(gen, vis_mode)
+        lib().orc_generate_rs(self.h, C.byref(c), C.byref(self.light), C.byref(g), int(pilot), float(d2_min),
+                              float(eps), _ptr(pos, C.c_double), _ptr(nrm, C.c_double), _ptr(flux, C.c_double),
+                              _ptr(tri, C.c_int64), _ptr(tag, C.c_int64), C.byref(info))
+        return dict(pos=pos[:M], nrm=nrm[:M], flux=flux[:M], tri=tri[:M], tag=tag[:M], paths=info.paths,
+                    m_far_kept=info.m_far_kept, cbar=info.a_rep, status=info.status)
 
     def light_vpls(self, n: int, seed: int) -> dict:
         """Direct term of Eq. 1 as n light-sample VPLs (orc_light_vpls);

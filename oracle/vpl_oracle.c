@@ -91,7 +91,7 @@ ORC_API void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uin
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-enum { STREAM_PATCH = 1, STREAM_LIGHT = 2, STREAM_IR = 3, STREAM_DIRECT = 4 };
+enum { STREAM_PATCH = 1, STREAM_LIGHT = 2, STREAM_IR = 3, STREAM_DIRECT = 4, STREAM_REJECT = 5 };
 
 static void rng4(uint64_t seed, uint64_t stream, uint64_t i, uint64_t j, uint64_t w[4])
 {
@@ -911,6 +911,138 @@ ORC_API void orc_gather(void *sp, int64_t n, const double *y, const double *ny,
  * analysis: term[i] (no visibility), vis[i] (1 visible, 0 blocked, -1 not
  * traced because term is zero), margin[i] (orc_segment_margin, only where
  * want_margin[i] != 0). */
+/* ------------------------------------------------------------------------ */
+/* Rejection-sampled instant radiosity (the comparison method the paper     */
+/* cites as r3): the light paths of plain instant radiosity, with no close   */
+/* range; every hit is a candidate VPL; its contribution to the image is     */
+/* estimated on a pilot grid of pixels (Eq. 1's pair term with visibility,   */
+/* the receiver's albedo and the path's albedos, channel mean); a candidate  */
+/* is kept with probability p = min(1, c / cbar), cbar the mean over the      */
+/* candidates of all ir_max_paths paths, decided by Philox (seed, 5) counter */
+/* (path, bounce); the first m_far kept in (path, bounce) order are the      */
+/* VPLs, P = last kept path + 1, flux = power x albedos / (P p).             */
+/* ------------------------------------------------------------------------ */
+ORC_API int64_t orc_generate_rs(void *sp, const ocamera *cam, const olight *L, const ogen *G, int32_t pilot,
+                                double d2min, double eps, double *pos, double *nrm, double *flux, int64_t *tri,
+                                int64_t *tag, oinfo *info)
+{
+    const oscene *s = (const oscene *)sp;
+    memset(info, 0, sizeof(*info));
+    const int64_t M = G->m_far, pmax = G->ir_max_paths, B = G->max_bounces;
+    for (int64_t i = 0; i < 3 * M; i++) pos[i] = nrm[i] = flux[i] = 0.0;
+    for (int64_t i = 0; i < M; i++) { tri[i] = -1; tag[i] = -1; }
+    /* candidates of every path, slot p * B + (b - 1) */
+    const int64_t ns = pmax * B;
+    d3 *cx = calloc((size_t)(ns > 0 ? ns : 1), sizeof(d3));
+    d3 *cn = calloc((size_t)(ns > 0 ? ns : 1), sizeof(d3));
+    double *ct = calloc((size_t)(ns > 0 ? 3 * ns : 1), sizeof(double));
+    int64_t *ck = malloc(sizeof(int64_t) * (size_t)(ns > 0 ? ns : 1));
+    double *cc = calloc((size_t)(ns > 0 ? ns : 1), sizeof(double));
+    for (int64_t i = 0; i < ns; i++) ck[i] = -1;
+    d3 nl = ld3(L->normal);
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < pmax; p++) {
+        uint64_t w[4];
+        rng4(G->seed, STREAM_IR, (uint64_t)p, 0, w);
+        d3 o, d;
+        if (L->type == 1) {
+            o = ld3(L->center);
+            d = sphere_dir(u01(w[2]), u01(w[3]));
+        } else {
+            o = light_point(L, u01(w[0]), u01(w[1]));
+            d = cosine_dir(nl, u01(w[2]), u01(w[3]));
+        }
+        double thr[3] = {1.0, 1.0, 1.0};
+        for (int64_t b = 1; b <= B; b++) {
+            double t;
+            int64_t k = closest(s, o, d, 0.0, &t, G->vis_mode);
+            if (k < 0) break;
+            if (!(dot(d, s->cr[k]) < 0.0)) break;   /* back face absorbs */
+            d3 x = add(o, scl(d, t));
+            for (int c = 0; c < 3; c++) thr[c] = thr[c] * s->rho[3 * k + c];
+            int64_t slot = p * B + (b - 1);
+            cx[slot] = x;
+            cn[slot] = s->n[k];
+            for (int c = 0; c < 3; c++) ct[3 * slot + c] = thr[c];
+            ck[slot] = k;
+            if (b == B) break;
+            rng4(G->seed, STREAM_IR, (uint64_t)p, (uint64_t)b, w);
+            d = cosine_dir(s->n[k], u01(w[0]), u01(w[1]));
+            o = add(x, scl(s->n[k], G->ray_eps));
+        }
+    }
+    /* pilot pixels: a pilot x ph grid over the same view */
+    const int64_t pw = pilot, ph0 = ((int64_t)pilot * cam->height + cam->width / 2) / cam->width;
+    const int64_t ph = ph0 > 0 ? ph0 : 1; /* round(pilot H / W), at least 1 */
+    ocamera pc = *cam;
+    pc.width = (int32_t)pw;
+    pc.height = (int32_t)ph;
+    const int64_t np = pw * ph;
+    int64_t *pix = malloc(sizeof(int64_t) * (size_t)np);
+    double *py = malloc(sizeof(double) * 3 * (size_t)np), *pn = malloc(sizeof(double) * 3 * (size_t)np);
+    double *pr = malloc(sizeof(double) * 3 * (size_t)np);
+    int64_t *pt = malloc(sizeof(int64_t) * (size_t)np);
+    for (int64_t q = 0; q < np; q++) pix[q] = q;
+    orc_gbuffer(sp, &pc, np, pix, G->vis_mode, py, pn, pr, pt);
+    d3 P = ld3(L->power);
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < ns; i++) {
+        if (ck[i] < 0) continue;
+        double acc = 0.0;
+        d3 q = add(cx[i], scl(cn[i], eps));
+        for (int64_t j = 0; j < np; j++) {
+            if (pt[j] < 0) continue;
+            d3 y = ld3(py + 3 * j), ny = ld3(pn + 3 * j);
+            double g = pair_term(y, ny, cx[i], cn[i], d2min);
+            if (g == 0.0) continue;
+            if (occluded(s, add(y, scl(ny, eps)), q, G->vis_mode)) continue;
+            double c = (pr[3 * j] * ct[3 * i] * P.x + pr[3 * j + 1] * ct[3 * i + 1] * P.y +
+                        pr[3 * j + 2] * ct[3 * i + 2] * P.z) / 3.0;
+            acc += g * c / PI;
+        }
+        cc[i] = acc;
+    }
+    double csum = 0.0;
+    int64_t nvalid = 0;
+    for (int64_t i = 0; i < ns; i++)
+        if (ck[i] >= 0) {
+            csum += cc[i];
+            nvalid++;
+        }
+    const double cbar = nvalid > 0 ? csum / (double)nvalid : 0.0;
+    /* acceptance in (path, bounce) order */
+    int64_t kept = 0, Pp = 0;
+    double *pk = malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
+    for (int64_t i = 0; i < ns && kept < M; i++) {
+        if (ck[i] < 0) continue;
+        int64_t p = i / B, b = i % B + 1;
+        uint64_t w[4];
+        rng4(G->seed, STREAM_REJECT, (uint64_t)p, (uint64_t)b, w);
+        double prob = cbar > 0.0 ? dmin(1.0, cc[i] / cbar) : 1.0;
+        if (!(u01(w[0]) < prob)) continue;
+        st3(pos + 3 * kept, cx[i]);
+        st3(nrm + 3 * kept, cn[i]);
+        st3(flux + 3 * kept, mk(ct[3 * i], ct[3 * i + 1], ct[3 * i + 2]));
+        tri[kept] = ck[i];
+        tag[kept] = p * 16 + b;
+        pk[kept] = prob;
+        kept++;
+        Pp = p + 1;
+    }
+    if (kept < M) { info->status = 7; Pp = pmax; }
+    info->paths = Pp;
+    info->m_far_kept = kept;
+    for (int64_t i = 0; i < kept; i++) {
+        double *fl = flux + 3 * i;
+        fl[0] = P.x * fl[0] / ((double)Pp * pk[i]);
+        fl[1] = P.y * fl[1] / ((double)Pp * pk[i]);
+        fl[2] = P.z * fl[2] / ((double)Pp * pk[i]);
+    }
+    info->a_rep = cbar; /* here: the mean candidate contribution */
+    free(cx); free(cn); free(ct); free(ck); free(cc); free(pix); free(py); free(pn); free(pr); free(pt); free(pk);
+    return kept;
+}
+
 ORC_API void orc_pairs(void *sp, const double *y, const double *ny, int64_t M, const double *x,
                        const double *nx, double d2min, double eps, int32_t vis_mode,
                        const uint8_t *want_margin, double *term, int8_t *vis, double *margin)

@@ -654,3 +654,71 @@ def test_set_sum_equals_point_rule_inside_single_faces(orc):
     b = o.generate(cam, W.GenParams(d_close=100.0, m_close=64, m_far=0, seed=9, patch_rule=1))
     same = (a["pos"] == b["pos"]).all(axis=1) & (a["flux"] == b["flux"]).all(axis=1)
     assert same.sum() >= 63 and np.array_equal(a["tri"][same], b["tri"][same])
+
+
+# ---------------------------------------------------------------------------
+# rejection-sampled instant radiosity (the comparison method cited as r3)
+# ---------------------------------------------------------------------------
+def _rs_view(seed=0, m=64):
+    import dataclasses
+    wl = W.cornell_workload()
+    v = wl.views[0]
+    gen = dataclasses.replace(v.gen, m_close=0, m_far=m, d_close=0.0, seed=seed)
+    return wl, v, gen
+
+
+def test_rs_vpls_are_ir_candidates_with_probabilities(orc):
+    """Every kept VPL is the hit (path, bounce) of plain instant radiosity's
+    walk -- same point, normal and face -- and its flux is the plain one
+    divided by its acceptance probability p in (0, 1] (the same p in every
+    channel); some VPLs were kept for sure (p = 1), some with p < 1."""
+    import dataclasses
+    wl, v, gen = _rs_view(seed=3)
+    o = orc.OracleScene(wl.scene)
+    rs = o.generate_rs(v.camera, gen, 8, v.gather.d2_min, v.gather.ray_eps, vis_mode=1)
+    assert rs["status"] == 0 and rs["m_far_kept"] == gen.m_far
+    big = dataclasses.replace(gen, m_far=3 * rs["paths"] + 3, ir_max_paths=rs["paths"])
+    ir = o.generate(v.camera, big, vis_mode=1)
+    assert (np.diff(rs["tag"]) > 0).all()
+    where = {int(t): k for k, t in enumerate(ir["tag"])}
+    ps = []
+    for k, t in enumerate(rs["tag"]):
+        j = where[int(t)]
+        assert np.array_equal(rs["pos"][k], ir["pos"][j]) and np.array_equal(rs["nrm"][k], ir["nrm"][j])
+        assert rs["tri"][k] == ir["tri"][j]
+        # flux_ir = power * albedos / P_ir (P_ir = ir paths), flux_rs = power * albedos / (P_rs p)
+        p = (ir["flux"][j] * ir["paths"]) / (rs["flux"][k] * rs["paths"])
+        assert np.allclose(p, p[0], rtol=1e-12) and 0.0 < p[0] <= 1.0 + 1e-12
+        ps.append(p[0])
+    ps = np.array(ps)
+    assert (ps > 1 - 1e-12).any() and (ps < 0.999).any()
+
+
+def test_rs_total_flux_matches_plain_ir_in_expectation(orc):
+    """Dividing by p keeps the estimator unbiased: over many seeds the mean
+    total flux of the kept VPLs equals plain instant radiosity's, within
+    four standard errors."""
+    rs, ir = [], []
+    wl, v, _ = _rs_view()
+    o = orc.OracleScene(wl.scene)
+    for seed in range(120):
+        _, _, gen = _rs_view(seed=seed)
+        rs.append(o.generate_rs(v.camera, gen, 8, v.gather.d2_min, v.gather.ray_eps, vis_mode=1)["flux"].sum(0))
+        ir.append(o.generate(v.camera, gen, vis_mode=1)["flux"].sum(0))
+    rs, ir = np.array(rs), np.array(ir)
+    se = np.sqrt(rs.var(0) / len(rs) + ir.var(0) / len(ir))
+    assert (np.abs(rs.mean(0) - ir.mean(0)) < 4 * se).all(), (rs.mean(0), ir.mean(0), se)
+
+
+def test_rs_keeps_only_vpls_that_light_the_pilot_pixels(orc):
+    """A candidate that reaches none of the pilot pixels has c = 0, p = 0."""
+    wl, v, gen = _rs_view(seed=5)
+    o = orc.OracleScene(wl.scene)
+    pilot = 8
+    rs = o.generate_rs(v.camera, gen, pilot, v.gather.d2_min, v.gather.ray_eps, vis_mode=1)
+    cam = v.camera
+    pc = W.Camera(cam.eye, cam.forward, cam.up, cam.vfov_deg, pilot, max(1, (pilot * cam.height + cam.width // 2) // cam.width))
+    gb = o.gbuffer(pc, vis_mode=1)
+    for k in range(len(rs["pos"])):
+        one = dict(pos=rs["pos"][k:k + 1], nrm=rs["nrm"][k:k + 1], flux=np.ones((1, 3)))
+        assert o.gather(gb, one, v.gather.d2_min, v.gather.ray_eps, vis_mode=1).sum() > 0, k
