@@ -215,6 +215,25 @@ VPL_API int vpl_generate(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam
  * streams, whichever of them wrote its record last). */
 VPL_API int vpl_generate_info(vpl_ctx *ctx, vpl_gen_info *out);
 
+/* Rejection-sampled instant radiosity, the comparison method the paper cites
+ * (Sec. 2, r3): VPLs of light paths that contribute little to the image are
+ * rejected.  The light paths are those of plain instant radiosity (no close
+ * range; gen->m_close must be 0, vpls->count == gen->m_far); every surface
+ * hit is a candidate whose contribution c to the image is estimated on a
+ * pilot grid of pilot x round(pilot * height / width) pixels over the same
+ * view (Eq. 1's pair term with visibility, d2_min and ray_eps as in the
+ * gather, the receiver's and the path's albedos, mean over the channels, in
+ * FP64); a candidate is kept with probability p = min(1, c / cbar), cbar the
+ * mean c over the candidates of all ir_max_paths paths, when the top 24 bits
+ * of Philox4x64-10 word 0 at key (seed, 5), counter (path, bounce, 0, 0) fall
+ * below p; the first m_far kept in (path, bounce) order are the VPLs, P = last
+ * kept path + 1, flux = power x albedos / (P p) (unbiased).  Tags and the
+ * report of vpl_generate_info as for vpl_generate; too few kept candidates
+ * latch VPL_ERR_PATHS_EXHAUSTED. */
+VPL_API int vpl_generate_rs(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam,
+                            const vpl_gen_params *gen, int32_t pilot, float d2_min, float ray_eps,
+                            const vpl_vpl_set *vpls, vpl_stream stream);
+
 /* Direct term L_e(y) of Eq. 1 (the light's own contribution, which the VPL
  * sum leaves out) as n light-sample VPLs written to vpls (count == n, either
  * format): sample k is the point c + (2 s1 - 1) edge_u / 2 + (2 s2 - 1)

@@ -480,6 +480,35 @@ int vpl_generate(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const 
     return VPL_OK;
 }
 
+int vpl_generate_rs(vpl_ctx *ctx, vpl_scene_id scene, const vpl_camera *cam, const vpl_gen_params *gen, int32_t pilot,
+                    float d2_min, float ray_eps, const vpl_vpl_set *vpls, vpl_stream stream)
+{
+    if (!ctx) return VPL_ERR_INVALID_ARG;
+    SceneRec *s = find_scene(ctx, scene);
+    if (!s) return fail(ctx, VPL_ERR_NOT_FOUND, "unknown scene id");
+    Frame F;
+    int rc = camera_frame(ctx, cam, &F);
+    if (rc) return rc;
+    if ((rc = check_gen(ctx, gen))) return rc;
+    if ((rc = check_vpls(ctx, vpls))) return rc;
+    if (gen->m_close != 0) return fail(ctx, VPL_ERR_INVALID_ARG, "rejection sampling makes far VPLs only: m_close must be 0");
+    if (vpls->count != gen->m_far) return fail(ctx, VPL_ERR_INVALID_ARG, "vpl set count must equal m_far");
+    if (pilot < 1 || pilot > 1024) return fail(ctx, VPL_ERR_INVALID_ARG, "pilot must be in [1, 1024]");
+    if (!(d2_min >= 0.0f) || !std::isfinite(d2_min) || !(ray_eps >= 0.0f) || !std::isfinite(ray_eps))
+        return fail(ctx, VPL_ERR_INVALID_ARG, "d2_min and ray_eps must be finite and >= 0");
+    vpl_camera pc = *cam;
+    pc.width = pilot;
+    const int64_t ph = ((int64_t)pilot * cam->height + cam->width / 2) / cam->width;
+    pc.height = (int32_t)(ph > 0 ? ph : 1);
+    Frame PF;
+    if ((rc = camera_frame(ctx, &pc, &PF))) return rc;
+    DeviceGuard g(ctx->device);
+    CK(ctx, generate_rs(exec_of(ctx, stream), view_of(s), gen_args(F, gen, s->light), cam_args(PF, &pc), d2_min,
+                        ray_eps, (float4 *)vpls->pos, vpls->nrm, vpls->flux, vpls->format, ctx->d_info),
+       "vpl_generate_rs");
+    return VPL_OK;
+}
+
 int vpl_light_vpls(vpl_ctx *ctx, vpl_scene_id scene, int32_t n, uint64_t seed, const vpl_vpl_set *vpls,
                    vpl_stream stream)
 {

@@ -354,7 +354,7 @@ __global__ void ir_walk_kernel(SceneView s, GenArgs g, const uint32_t *close_fla
         thr[0] = thr[0] * (double)rho.x;
         thr[1] = thr[1] * (double)rho.y;
         thr[2] = thr[2] * (double)rho.z;
-        if (!close_flag[k]) {
+        if (!close_flag || !close_flag[k]) {
             int64_t slot = p * B + (b - 1);
             c_pos[slot] = make_float4(x.x, x.y, x.z, __int_as_float(k));
             c_nrm[slot] = make_float4(nk.x, nk.y, nk.z, __int_as_float((int)(p * 16 + b)));
@@ -409,6 +409,187 @@ __global__ void far_tail_kernel(GenArgs g, const GenInfoDev *info, float4 *pos, 
     if (i >= g.m_far || i < info->m_far_kept) return;
     const float3 z = make_float3(0.0f, 0.0f, 0.0f);
     store_vpl(pos, nrm, flux, g.m_close + i, z, -1, z, -1, z, fmt);
+}
+
+// ---------------------------------------------------------------------------
+// Rejection-sampled instant radiosity (the comparison method the paper cites
+// as r3): the light paths of plain instant radiosity with no close range;
+// every hit is a candidate; its contribution c to the image is estimated on a
+// pilot grid of pixels (Eq. 1's pair term with visibility, the receiver's and
+// the path's albedos, channel mean, FP64); a candidate is kept with
+// probability p = min(1, c / cbar), cbar the mean over all candidates, decided
+// by Philox (seed, 5) counter (path, bounce); the first m_far kept in (path,
+// bounce) order are the VPLs, P = last kept path + 1, flux = power x albedos
+// / (P p).
+// ---------------------------------------------------------------------------
+constexpr int kRsThreads = 256;
+
+// block per candidate slot, threads over the pilot pixels (fixed-order sums)
+__global__ void __launch_bounds__(kRsThreads) rs_contrib_kernel(SceneView s, GenArgs g, const float4 *c_pos,
+                                                                const float4 *c_nrm, const double *c_thr,
+                                                                const uint32_t *c_valid, const float4 *p_pos,
+                                                                const float4 *p_nrm, const float4 *p_alb, int np,
+                                                                float d2min, float eps, double *contrib, int *status)
+{
+    __shared__ double part[kRsThreads];
+    const int64_t slot = blockIdx.x;
+    if (!c_valid[slot]) {
+        if (threadIdx.x == 0) contrib[slot] = 0.0;
+        return;
+    }
+    const float4 cx = c_pos[slot], cn4 = c_nrm[slot];
+    const D3 x = dmk(cx.x, cx.y, cx.z), nx = dmk(cn4.x, cn4.y, cn4.z);
+    const float3 q = fma3(f3(cn4), eps, f3(cx));
+    const double w[3] = {c_thr[3 * slot] * (double)g.light.power[0], c_thr[3 * slot + 1] * (double)g.light.power[1],
+                         c_thr[3 * slot + 2] * (double)g.light.power[2]};
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < np; j += kRsThreads) {
+        const float4 py = p_pos[j];
+        if (__float_as_int(py.w) < 0) continue;
+        const float4 pn = p_nrm[j];
+        const D3 y = dmk(py.x, py.y, py.z), ny = dmk(pn.x, pn.y, pn.z);
+        const D3 d = dsub(x, y);
+        const double d2 = ddot(d, d);
+        if (d2 == 0.0) continue;
+        const double dl = __dsqrt_rn(d2);
+        const double cy = ddot(ny, d) / dl, ci = -ddot(nx, d) / dl;
+        if (!(cy > 0.0) || !(ci > 0.0)) continue;
+        const float3 o = fma3(f3(pn), eps, f3(py));
+        if (occluded1(s, make_ray(o, q - o), status)) continue;
+        const double gterm = ci * cy / (kPiD * fmax(d2, (double)d2min));
+        const float4 a = p_alb[j];
+        const double c = ((double)a.x * w[0] + (double)a.y * w[1] + (double)a.z * w[2]) / 3.0;
+        acc += gterm * c / kPiD;
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = kRsThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) contrib[slot] = part[0];
+}
+
+// fixed-order sums of the contributions and counts of valid candidates
+__global__ void __launch_bounds__(kRsThreads) rs_sum_kernel(const double *contrib, const uint32_t *c_valid,
+                                                            int64_t n, double *psum, unsigned long long *pcnt)
+{
+    __shared__ double ps[kRsThreads];
+    __shared__ unsigned long long pc[kRsThreads];
+    double a = 0.0;
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kRsThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRsThreads)
+        if (c_valid[i]) {
+            a += contrib[i];
+            c++;
+        }
+    ps[threadIdx.x] = a;
+    pc[threadIdx.x] = c;
+    __syncthreads();
+    for (int h = kRsThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            ps[threadIdx.x] += ps[threadIdx.x + h];
+            pc[threadIdx.x] += pc[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        psum[blockIdx.x] = ps[0];
+        pcnt[blockIdx.x] = pc[0];
+    }
+}
+
+__global__ void rs_accept_kernel(GenArgs g, const double *contrib, uint32_t *c_valid, const double *psum,
+                                 const unsigned long long *pcnt, int nparts, int64_t n, double *prob)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !c_valid[i]) return;
+    double sum = 0.0;
+    unsigned long long cnt = 0;
+    for (int k = 0; k < nparts; k++) { // the same order in every thread
+        sum += psum[k];
+        cnt += pcnt[k];
+    }
+    const double cbar = cnt ? sum / (double)cnt : 0.0;
+    const double pr = cbar > 0.0 ? fmin(1.0, contrib[i] / cbar) : 1.0;
+    const int64_t B = g.max_bounces, p = i / B, b = i % B + 1;
+    uint64_t w[4];
+    rng4(g.seed, kStreamReject, (uint64_t)p, (uint64_t)b, w);
+    prob[i] = pr;
+    c_valid[i] = u01(w[0]) < pr ? 1u : 0u;
+}
+
+__global__ void rs_emit_kernel(GenArgs g, const float4 *c_pos, const float4 *c_nrm, const double *c_thr,
+                               const uint32_t *c_valid, const uint32_t *rank, const double *prob, int64_t n_slots,
+                               const GenInfoDev *info, float4 *pos, void *nrm, void *flux, int fmt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slots || !c_valid[i] || rank[i] >= (uint32_t)g.m_far) return;
+    const int64_t v = rank[i];
+    const double d = (double)info->paths * prob[i];
+    const float4 cp = c_pos[i], cn = c_nrm[i];
+    store_vpl(pos, nrm, flux, v, f3(cp), __float_as_int(cp.w), f3(cn), __float_as_int(cn.w),
+              make_float3((float)(g.light.power[0] * c_thr[3 * i] / d), (float)(g.light.power[1] * c_thr[3 * i + 1] / d),
+                          (float)(g.light.power[2] * c_thr[3 * i + 2] / d)),
+              fmt);
+}
+
+cudaError_t generate_rs(const Exec &ex, const SceneView &s, const GenArgs &g, const CamArgs &pilot, float d2min,
+                        float eps, float4 *pos, void *nrm, void *flux, int fmt, GenInfoDev *report)
+{
+    const int TB = kGenThreads;
+    Tmp rec;
+    VPL_TRY(rec.alloc(ex, sizeof(GenInfoDev)));
+    GenInfoDev *info = rec.as<GenInfoDev>();
+    VPL_TRY(cudaMemsetAsync(info, 0, sizeof(GenInfoDev), ex.stream));
+    if (g.m_far > 0) {
+        const int64_t n_paths = g.max_paths, n_slots = n_paths * g.max_bounces;
+        const int np = pilot.width * pilot.height;
+        Tmp cp, cn, ct, cv, rk, pp, pn, pa, cc, pr, ps, pc;
+        VPL_TRY(cp.alloc(ex, sizeof(float4) * n_slots));
+        VPL_TRY(cn.alloc(ex, sizeof(float4) * n_slots));
+        VPL_TRY(ct.alloc(ex, sizeof(double) * 3 * n_slots));
+        VPL_TRY(cv.alloc(ex, sizeof(uint32_t) * n_slots));
+        VPL_TRY(rk.alloc(ex, sizeof(uint32_t) * (n_slots + 1)));
+        VPL_TRY(pp.alloc(ex, sizeof(float4) * np));
+        VPL_TRY(pn.alloc(ex, sizeof(float4) * np));
+        VPL_TRY(pa.alloc(ex, sizeof(float4) * np));
+        VPL_TRY(cc.alloc(ex, sizeof(double) * n_slots));
+        VPL_TRY(pr.alloc(ex, sizeof(double) * n_slots));
+        const int nparts = 256;
+        VPL_TRY(ps.alloc(ex, sizeof(double) * nparts));
+        VPL_TRY(pc.alloc(ex, sizeof(unsigned long long) * nparts));
+        ir_walk_kernel<<<grid_for(n_paths, TB), TB, 0, ex.stream>>>(s, g, nullptr, n_paths, cp.as<float4>(),
+                                                                    cn.as<float4>(), ct.as<double>(),
+                                                                    cv.as<uint32_t>(), ex.status);
+        VPL_LAUNCHED(ex);
+        VPL_TRY(gbuffer_build(ex, s, pilot, false, pp.as<float4>(), pn.p, pa.p, VPL_FORMAT_FP32));
+        rs_contrib_kernel<<<(unsigned)n_slots, kRsThreads, 0, ex.stream>>>(
+            s, g, cp.as<float4>(), cn.as<float4>(), ct.as<double>(), cv.as<uint32_t>(), pp.as<float4>(),
+            pn.as<float4>(), pa.as<float4>(), np, d2min, eps, cc.as<double>(), ex.status);
+        VPL_LAUNCHED(ex);
+        rs_sum_kernel<<<nparts, kRsThreads, 0, ex.stream>>>(cc.as<double>(), cv.as<uint32_t>(), n_slots,
+                                                            ps.as<double>(), pc.as<unsigned long long>());
+        VPL_LAUNCHED(ex);
+        rs_accept_kernel<<<grid_for(n_slots, 256), 256, 0, ex.stream>>>(g, cc.as<double>(), cv.as<uint32_t>(),
+                                                                        ps.as<double>(), pc.as<unsigned long long>(),
+                                                                        nparts, n_slots, pr.as<double>());
+        VPL_LAUNCHED(ex);
+        VPL_TRY(exclusive_scan<uint32_t>(ex, cv.as<uint32_t>(), rk.as<uint32_t>(), nullptr, n_slots));
+        ir_paths_kernel<<<grid_for(n_slots, 256), 256, 0, ex.stream>>>(cv.as<uint32_t>(), rk.as<uint32_t>(), n_slots,
+                                                                       g.max_bounces, g.m_far, n_paths, info,
+                                                                       ex.status);
+        VPL_LAUNCHED(ex);
+        rs_emit_kernel<<<grid_for(n_slots, 256), 256, 0, ex.stream>>>(g, cp.as<float4>(), cn.as<float4>(),
+                                                                      ct.as<double>(), cv.as<uint32_t>(),
+                                                                      rk.as<uint32_t>(), pr.as<double>(), n_slots,
+                                                                      info, pos, nrm, flux, fmt);
+        VPL_LAUNCHED(ex);
+        far_tail_kernel<<<grid_for(g.m_far, 256), 256, 0, ex.stream>>>(g, info, pos, nrm, flux, fmt);
+        VPL_LAUNCHED(ex);
+    }
+    if (report) VPL_TRY(cudaMemcpyAsync(report, info, sizeof(GenInfoDev), cudaMemcpyDeviceToDevice, ex.stream));
+    return cudaSuccess;
 }
 
 // Direct term L_e(y) of Eq. 1 as light-sample VPLs: sample k is the point of

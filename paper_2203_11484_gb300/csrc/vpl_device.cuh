@@ -125,7 +125,7 @@ __device__ __forceinline__ TriD tri_exact(const SceneView &s, int32_t t)
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (i, j, 0, 0),
 // key (seed, stream)
 // --------------------------------------------------------------------------
-enum { kStreamPatch = 1, kStreamLight = 2, kStreamIR = 3, kStreamDirect = 4 };
+enum { kStreamPatch = 1, kStreamLight = 2, kStreamIR = 3, kStreamDirect = 4, kStreamReject = 5 };
 
 __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1)
 {

@@ -104,6 +104,9 @@ cudaError_t generate_vpls(const Exec &ex, const SceneView &s, const GenArgs &g, 
                           void *nrm, void *flux, int format, GenInfoDev *report);
 cudaError_t light_vpls(const Exec &ex, const LightView &L, int n, uint64_t seed, float4 *pos, void *nrm, void *flux,
                        int fmt);
+struct CamArgs;
+cudaError_t generate_rs(const Exec &ex, const SceneView &s, const GenArgs &g, const CamArgs &pilot, float d2min,
+                        float eps, float4 *pos, void *nrm, void *flux, int fmt, GenInfoDev *report);
 
 // ---- gather.cu -----------------------------------------------------------------
 struct CamArgs {

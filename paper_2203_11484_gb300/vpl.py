@@ -90,6 +90,8 @@ _SIGS = {
     "vpl_scene_query": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_scene_info)]),
     "vpl_gbuffer_build": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_camera), C.POINTER(vpl_gbuffer), _P]),
     "vpl_light_vpls": (C.c_int, [_P, C.c_uint64, C.c_int32, C.c_uint64, C.POINTER(vpl_vpl_set), _P]),
+    "vpl_generate_rs": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_camera), C.POINTER(vpl_gen_params), C.c_int32,
+                                  C.c_float, C.c_float, C.POINTER(vpl_vpl_set), _P]),
     "vpl_generate": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_camera), C.POINTER(vpl_gen_params),
                                C.POINTER(vpl_vpl_set), _P]),
     "vpl_generate_info": (C.c_int, [_P, C.POINTER(vpl_gen_info)]),
@@ -306,6 +308,13 @@ def vpl_gbuffer_build(ctx, scene: int, camera: W.Camera, gbuf: GBuffer, stream=N
     cam, gb = make_camera(camera), gbuf.struct()
     _check(ctx, load().vpl_gbuffer_build(ctx, scene, C.byref(cam), C.byref(gb), _stream(stream)),
            "vpl_gbuffer_build")
+
+
+def vpl_generate_rs(ctx, scene: int, camera: W.Camera, gen: W.GenParams, pilot: int, d2_min: float,
+                    ray_eps: float, vpls: VplSet, stream=None) -> None:
+    cam, g, vs = make_camera(camera), make_gen(gen), vpls.struct()
+    _check(ctx, load().vpl_generate_rs(ctx, scene, C.byref(cam), C.byref(g), int(pilot), float(d2_min),
+                                       float(ray_eps), C.byref(vs), _stream(stream)), "vpl_generate_rs")
 
 
 def vpl_light_vpls(ctx, scene: int, n: int, seed: int, vpls: VplSet, stream=None) -> None:
