@@ -1,14 +1,16 @@
 """Quality study of the hybrid sampler against plain instant radiosity.
 
-The paper (Sec. 4) compares its hybrid VPL sampling with instant radiosity on
+The paper (Sec. 4) compares its hybrid VPL sampling with instant radiosity and
+rejection sampling (among others) on
 close-up views: the RMSE of the indirect image against a reference made by
 densely sampled instant radiosity (more than 200k VPLs) at equal VPL counts,
 and the VPL count and time each method needs for equal RMSE.  This module
 runs that comparison on the synthetic scenes through the library's own
 calls: the hybrid is alpha * M patch VPLs plus the rest from light paths,
 plain instant radiosity is m_close = 0 with no close range (d_close = 0: every
-light-path hit is a VPL), the reference is plain instant radiosity with many
-VPLs.  Indirect light only,
+light-path hit is a VPL), the rejection sampling is vpl_generate_rs (plain light paths, candidates kept
+in proportion to their estimated contribution), the reference is plain
+instant radiosity with many VPLs.  Indirect light only,
 as in the paper.  Light: the scene's square light, or a point light at its
 centre with the same power (the paper's scenes use point lights).
 
@@ -66,6 +68,22 @@ def study(view: W.View, scene: W.Scene, ms: Sequence[int] = (1024, 2048, 4096, 8
         gb = V.GBuffer.empty(cam.width, cam.height)
         V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
 
+        def render_rs(m: int, seed: int):
+            # rejection-sampled instant radiosity (no close range), pilot 32 x 32
+            gen = dataclasses.replace(view.gen, m_close=0, m_far=m, seed=seed, d_close=0.0)
+            vs = V.VplSet.empty(m)
+            out = torch.zeros((npx, 4), dtype=torch.float32, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            V.vpl_generate_rs(ctx.h, sid, cam, gen, 32, gat.d2_min, gat.ray_eps, vs)
+            V.vpl_gather(ctx.h, sid, gb, vs, gat, out)
+            e1.record()
+            torch.cuda.synchronize()
+            rc = V.vpl_sync(ctx.h, check=False)
+            if rc != 0:
+                raise RuntimeError(f"device status {rc} in rejection sampling, m={m}")
+            return out, e0.elapsed_time(e1)
+
         def render(m_close: int, m_far: int, seed: int):
             # plain instant radiosity has no close range: d_close = 0 keeps every
             # light-path hit (with d_close > 0, m_close = 0 would still drop the
@@ -96,7 +114,7 @@ def study(view: W.View, scene: W.Scene, ms: Sequence[int] = (1024, 2048, 4096, 8
                 mc, mf = W.split_budget(m, frac)
                 errs, times = [], []
                 for s in range(seeds):
-                    img, t = render(mc, mf, 100 + s)
+                    img, t = render_rs(m, 100 + s) if label == "rejection sampling" else render(mc, mf, 100 + s)
                     errs.append(_rmse(img, ref))
                     times.append(t)
                 rows.append({"method": label, "vpls": m, "m_close": mc, "m_far": mf,
@@ -106,6 +124,7 @@ def study(view: W.View, scene: W.Scene, ms: Sequence[int] = (1024, 2048, 4096, 8
 
         hyb = curve("hybrid", ms, alpha)
         ir = curve("instant radiosity", ir_ms, 0.0)
+        rs = curve("rejection sampling", ms, 0.0)
         ir_m = [r["vpls"] for r in ir]
         ir_e = [r["rmse"] for r in ir]
         ir_t = [r["ms"] for r in ir]
@@ -116,7 +135,8 @@ def study(view: W.View, scene: W.Scene, ms: Sequence[int] = (1024, 2048, 4096, 8
             equal.append({"hybrid_vpls": r["vpls"], "rmse": r["rmse"], "ir_vpls_for_equal_rmse": m_ir,
                           "vpl_ratio": m_ir / r["vpls"], "time_ratio": t_ir / r["ms"]})
         same_m = [{"vpls": r["vpls"], "rmse_hybrid": r["rmse"],
-                   "rmse_ir": next(q["rmse"] for q in ir if q["vpls"] == r["vpls"])}
+                   "rmse_ir": next(q["rmse"] for q in ir if q["vpls"] == r["vpls"]),
+                   "rmse_rs": next(q["rmse"] for q in rs if q["vpls"] == r["vpls"])}
                   for r in hyb if r["vpls"] in ir_m]
         for row in same_m:
             row["ir_over_hybrid"] = row["rmse_ir"] / row["rmse_hybrid"]
@@ -129,7 +149,8 @@ def study(view: W.View, scene: W.Scene, ms: Sequence[int] = (1024, 2048, 4096, 8
         V.vpl_scene_release(ctx.h, sid)
         return {"reference": {"method": "instant radiosity", "vpls": m_ref * ref_renders, "ms_each": ref_ms,
                               "mean": float(ref[:, :3].double().mean())}, "hybrid_large": bias,
-                "hybrid": hyb, "instant_radiosity": ir, "equal_vpls": same_m, "equal_rmse": equal,
+                "hybrid": hyb, "instant_radiosity": ir, "rejection_sampling": rs, "equal_vpls": same_m,
+                "equal_rmse": equal,
                 "pixels": npx, "seeds": seeds, "alpha": alpha}
     finally:
         if own:
@@ -147,9 +168,11 @@ def point_light_scene(scene: W.Scene) -> W.Scene:
 def markdown(res: Dict, title: str) -> str:
     lines = [f"{title}: reference = instant radiosity with {res['reference']['vpls']} VPLs, "
              f"{res['pixels']} pixels, mean of {res['seeds']} seeds", "",
-             "| VPLs | RMSE hybrid | RMSE instant radiosity | IR / hybrid |", "|---:|---:|---:|---:|"]
+             "| VPLs | RMSE hybrid | RMSE instant radiosity | RMSE rejection sampling | IR / hybrid |",
+             "|---:|---:|---:|---:|---:|"]
     for r in res["equal_vpls"]:
-        lines.append(f"| {r['vpls']} | {r['rmse_hybrid']:.3g} | {r['rmse_ir']:.3g} | {r['ir_over_hybrid']:.2f} |")
+        lines.append(f"| {r['vpls']} | {r['rmse_hybrid']:.3g} | {r['rmse_ir']:.3g} | {r['rmse_rs']:.3g} | "
+                     f"{r['ir_over_hybrid']:.2f} |")
     lines += ["", "| hybrid VPLs | RMSE | IR VPLs for that RMSE | VPL ratio | time ratio |", "|---:|---:|---:|---:|---:|"]
     for r in res["equal_rmse"]:
         m = r["ir_vpls_for_equal_rmse"]

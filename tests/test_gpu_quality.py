@@ -22,6 +22,7 @@ def test_quality_study_small(light):
     res = Q.study(wl.views[0], scene, ms=(256, 1024), ir_ms=(256, 1024, 4096), seeds=2, m_ref=16384, ref_renders=2,
                   bias_m=8192)
     ir = [r["rmse"] for r in res["instant_radiosity"]]
+    assert all(math.isfinite(r["rmse"]) for r in res["rejection_sampling"])
     hy = [r["rmse"] for r in res["hybrid"]]
     assert all(math.isfinite(e) and e > 0 for e in ir + hy)
     assert ir[-1] < ir[0] and hy[-1] < hy[0]
