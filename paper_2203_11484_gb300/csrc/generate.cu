@@ -499,18 +499,24 @@ __global__ void __launch_bounds__(kRsThreads) rs_sum_kernel(const double *contri
     }
 }
 
-__global__ void rs_accept_kernel(GenArgs g, const double *contrib, uint32_t *c_valid, const double *psum,
-                                 const unsigned long long *pcnt, int nparts, int64_t n, double *prob)
+// cbar: the partial sums added in a fixed order
+__global__ void rs_mean_kernel(const double *psum, const unsigned long long *pcnt, int nparts, double *cbar)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !c_valid[i]) return;
     double sum = 0.0;
     unsigned long long cnt = 0;
-    for (int k = 0; k < nparts; k++) { // the same order in every thread
+    for (int k = 0; k < nparts; k++) {
         sum += psum[k];
         cnt += pcnt[k];
     }
-    const double cbar = cnt ? sum / (double)cnt : 0.0;
+    *cbar = cnt ? sum / (double)cnt : 0.0;
+}
+
+__global__ void rs_accept_kernel(GenArgs g, const double *contrib, uint32_t *c_valid, const double *cbar_p, int64_t n,
+                                 double *prob)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !c_valid[i]) return;
+    const double cbar = *cbar_p;
     const double pr = cbar > 0.0 ? fmin(1.0, contrib[i] / cbar) : 1.0;
     const int64_t B = g.max_bounces, p = i / B, b = i % B + 1;
     uint64_t w[4];
@@ -557,7 +563,7 @@ cudaError_t generate_rs(const Exec &ex, const SceneView &s, const GenArgs &g, co
         VPL_TRY(cc.alloc(ex, sizeof(double) * n_slots));
         VPL_TRY(pr.alloc(ex, sizeof(double) * n_slots));
         const int nparts = 256;
-        VPL_TRY(ps.alloc(ex, sizeof(double) * nparts));
+        VPL_TRY(ps.alloc(ex, sizeof(double) * (nparts + 1))); // partial sums, then cbar
         VPL_TRY(pc.alloc(ex, sizeof(unsigned long long) * nparts));
         ir_walk_kernel<<<grid_for(n_paths, TB), TB, 0, ex.stream>>>(s, g, nullptr, n_paths, cp.as<float4>(),
                                                                     cn.as<float4>(), ct.as<double>(),
@@ -571,9 +577,12 @@ cudaError_t generate_rs(const Exec &ex, const SceneView &s, const GenArgs &g, co
         rs_sum_kernel<<<nparts, kRsThreads, 0, ex.stream>>>(cc.as<double>(), cv.as<uint32_t>(), n_slots,
                                                             ps.as<double>(), pc.as<unsigned long long>());
         VPL_LAUNCHED(ex);
+        rs_mean_kernel<<<1, 1, 0, ex.stream>>>(ps.as<double>(), pc.as<unsigned long long>(), nparts,
+                                               ps.as<double>() + nparts);
+        VPL_LAUNCHED(ex);
         rs_accept_kernel<<<grid_for(n_slots, 256), 256, 0, ex.stream>>>(g, cc.as<double>(), cv.as<uint32_t>(),
-                                                                        ps.as<double>(), pc.as<unsigned long long>(),
-                                                                        nparts, n_slots, pr.as<double>());
+                                                                        ps.as<double>() + nparts, n_slots,
+                                                                        pr.as<double>());
         VPL_LAUNCHED(ex);
         VPL_TRY(exclusive_scan<uint32_t>(ex, cv.as<uint32_t>(), rk.as<uint32_t>(), nullptr, n_slots));
         ir_paths_kernel<<<grid_for(n_slots, 256), 256, 0, ex.stream>>>(cv.as<uint32_t>(), rk.as<uint32_t>(), n_slots,
