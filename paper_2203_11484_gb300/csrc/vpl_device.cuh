@@ -522,6 +522,10 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     const unsigned long long sx2 = pack2(r.inv.x, r.inv.x), cx2 = pack2(-r.oinv.x, -r.oinv.x);
     const unsigned long long sy2 = pack2(r.inv.y, r.inv.y), cy2 = pack2(-r.oinv.y, -r.oinv.y);
     const unsigned long long sz2 = pack2(r.inv.z, r.inv.z), cz2 = pack2(-r.oinv.z, -r.oinv.z);
+    // lanes with nothing to test get plane offsets of 3e38: every entry
+    // parameter is huge, so their slab tests fail without a predicate
+    unsigned long long kx2 = cx2, ky2 = cy2, kz2 = cz2;
+    if (!(want && !occl)) kx2 = ky2 = kz2 = pack2(3.0e38f, 3.0e38f);
     int sp = 0, node = 0, steps = 0;
     while (true) {
         Node4 n;
@@ -530,15 +534,15 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
         if (oriented) {
             const float4 *p = s.nodes + 8 * (int64_t)node;
             // plane crossings of all four children, two per instruction
-            const float4 ex = fma4(__ldg(p + fx), sx2, cx2), xx = fma4(__ldg(p + (fx ^ 1)), sx2, cx2);
-            const float4 ey = fma4(__ldg(p + fy), sy2, cy2), xy = fma4(__ldg(p + (fy ^ 1)), sy2, cy2);
-            const float4 ez = fma4(__ldg(p + fz), sz2, cz2), xz = fma4(__ldg(p + (fz ^ 1)), sz2, cz2);
+            const float4 ex = fma4(__ldg(p + fx), sx2, kx2), xx = fma4(__ldg(p + (fx ^ 1)), sx2, kx2);
+            const float4 ey = fma4(__ldg(p + fy), sy2, ky2), xy = fma4(__ldg(p + (fy ^ 1)), sy2, ky2);
+            const float4 ez = fma4(__ldg(p + fz), sz2, kz2), xz = fma4(__ldg(p + (fz ^ 1)), sz2, kz2);
             load_node4_meta(p, n);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const float te = fmax3(comp(ex, k), comp(ey, k), fmaxf(comp(ez, k), 0.0f));
                 const float tx = fmin3(comp(xx, k), comp(xy, k), fminf(comp(xz, k), 1.0f));
-                if (live && te <= tx) hits |= 1u << k;
+                if (te <= tx) hits |= 1u << k;
             }
         } else {
             load_node4(s.nodes, node, n);
@@ -572,6 +576,7 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
                             occl = true;
                             cache2 = cache;
                             cache = q;
+                            kx2 = ky2 = kz2 = pack2(3.0e38f, 3.0e38f);
                         }
                     }
                 }
