@@ -178,9 +178,21 @@ def cpu_baseline(workload, seconds: float = 12.0) -> dict:
             break
         # grow the sample towards the time budget
         n = int(min(4096, max(n, n * 0.5 * (seconds - t_used) / max(dt, 1e-3))))
-    return {"value": pairs / t_used, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same on one core, a shorter sample
+    one = None
+    try:
+        oracle.set_threads(1)
+        pix = rng.choice(cam.width * cam.height, 256, replace=False)
+        t0 = time.perf_counter()
+        oracle.render(osc, view, pix)
+        one = 256 * M / (time.perf_counter() - t0)
+    finally:
+        oracle.set_threads(cores)
+    return {"value": pairs / t_used, "unit": UNIT, "cores": cores, "kind": "oracle", "value_1core": one,
             "sample": f"{runs} oracle renders (FP64, own BVH) of {pairs // M} sampled pixels x {M} VPLs "
-                      f"incl. G-buffer of those pixels and full VPL generation, {t_used:.1f} s"}
+                      f"incl. G-buffer of those pixels and full VPL generation, {t_used:.1f} s; "
+                      f"value_1core: 256 pixels on one thread"}
 
 
 def batch_section(ctx, n_views: int, precision: int, reps: int = 2) -> dict:

@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
             L.orc_light_vpls.argtypes = [C.POINTER(_Light), C.c_int64, C.c_uint64, _D, _D, _D, _I64]
             L.orc_light_vpls.restype = C.c_int64
             L.orc_num_threads.restype = C.c_int32
+            L.orc_set_threads.argtypes = [C.c_int32]
             _lib = L
     return _lib
 
@@ -116,6 +117,11 @@ def _ptr(a: np.ndarray, ct):
 def _f64(a, shape=None) -> np.ndarray:
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
     return a if shape is None else a.reshape(shape)
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on."""
+    lib().orc_set_threads(int(n))
 
 
 def num_threads() -> int:

@@ -1064,6 +1064,16 @@ ORC_API void orc_pairs(void *sp, const double *y, const double *ny, int64_t M, c
     }
 }
 
+/* threads of the parallel loops from now on (n >= 1) */
+ORC_API void orc_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 ORC_API int32_t orc_num_threads(void)
 {
 #ifdef _OPENMP
