@@ -30,7 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "pixel-VPL contributions/s with visibility"
+# the headline value is the first quantity (pairs/s); batched views/s and the
+# serving p99 latencies are in the line's "batch" and "serving" objects
+METRIC = "pixel-VPL contributions/s with visibility; batched views/s and p99 latency"
 UNIT = "pairs/s"
 
 # executed FP32 operations per unit of gather work, counted from the source of
