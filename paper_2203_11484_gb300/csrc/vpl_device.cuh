@@ -483,42 +483,15 @@ struct WarpCounters {
     uint32_t steps;         // per warp: packet traversal steps (same in every lane)
 };
 
-// `cache`, `cache2` (per lane) are the triangle slots of the last two
-// triangles that blocked one of this lane's segments (most recent first), or
-// -1.  They are tested before the traversal: neighbouring VPLs are usually
-// hidden by the same triangle.  The answer is the same with or without them
-// (a segment is blocked when any triangle blocks it).
-template <bool COUNT>
-__device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, const Ray &r, int &cache,
-                                              int &cache2, int *stk, int *status, WarpCounters &wc)
+// The packet walk proper; ORIENTED (all live segments share direction
+// signs) and the general case are separate instantiations, so each keeps
+// only the ray values its slab test reads.
+template <bool COUNT, bool ORIENTED>
+__device__ __forceinline__ bool packet_walk(const SceneView &s, bool want, const Ray &r, bool occl, int &cache,
+                                            int &cache2, int *stk, int *status, WarpCounters &wc, int fx, int fy,
+                                            int fz)
 {
     const int lane = threadIdx.x & 31;
-    bool occl = false;
-    if (want && cache >= 0) {
-        if (COUNT) wc.tests++;
-        if (seg_block(r, __ldg(s.tri + 3 * cache), __ldg(s.tri + 3 * cache + 1), __ldg(s.tri + 3 * cache + 2)))
-            occl = true;
-    }
-    if (want && !occl && cache2 >= 0) {
-        if (COUNT) wc.tests++;
-        if (seg_block(r, __ldg(s.tri + 3 * cache2), __ldg(s.tri + 3 * cache2 + 1), __ldg(s.tri + 3 * cache2 + 2))) {
-            occl = true;
-            const int x = cache; cache = cache2; cache2 = x;
-        }
-    }
-    unsigned alive = __ballot_sync(kFull, want && !occl);
-    if (alive == 0) return occl;
-    // Direction signs of the live segments, per axis.  When every live segment
-    // of the packet points the same way along an axis, the entry plane of that
-    // axis is the same box face for all of them, so the packet loads the near
-    // and far rows by address and skips the per-lane min/max that orders the
-    // two plane crossings (the usual case: 32 pixels of a small tile seen from
-    // one VPL).  Otherwise it takes the general slab test.
-    const unsigned nx = __ballot_sync(kFull, want && !occl && signbit(r.inv.x));
-    const unsigned ny = __ballot_sync(kFull, want && !occl && signbit(r.inv.y));
-    const unsigned nz = __ballot_sync(kFull, want && !occl && signbit(r.inv.z));
-    const bool oriented = (nx == 0 || nx == alive) && (ny == 0 || ny == alive) && (nz == 0 || nz == alive);
-    const int fx = nx ? 1 : 0, fy = ny ? 3 : 2, fz = nz ? 5 : 4; // row of each axis' entry plane
     const unsigned long long sx2 = pack2(r.inv.x, r.inv.x), cx2 = pack2(-r.oinv.x, -r.oinv.x);
     const unsigned long long sy2 = pack2(r.inv.y, r.inv.y), cy2 = pack2(-r.oinv.y, -r.oinv.y);
     const unsigned long long sz2 = pack2(r.inv.z, r.inv.z), cz2 = pack2(-r.oinv.z, -r.oinv.z);
@@ -531,7 +504,7 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
         Node4 n;
         const bool live = want && !occl;
         unsigned hits = 0;     // children this lane's segment enters
-        if (oriented) {
+        if (ORIENTED) {
             const float4 *p = s.nodes + 8 * (int64_t)node;
             // plane crossings of all four children, two per instruction
             const float4 ex = fma4(__ldg(p + fx), sx2, kx2), xx = fma4(__ldg(p + (fx ^ 1)), sx2, kx2);
@@ -581,8 +554,7 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
                     }
                 }
             }
-            alive = __ballot_sync(kFull, want && !occl);
-            if (alive == 0) break;
+            if (__ballot_sync(kFull, want && !occl) == 0) break;
             any = __reduce_or_sync(kFull, occl ? 0u : hits);
         }
         unsigned need = any & n.intmask;
@@ -605,6 +577,45 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     }
     __syncwarp();
     return occl;
+}
+
+// `cache`, `cache2` (per lane) are the triangle slots of the last two
+// triangles that blocked one of this lane's segments (most recent first), or
+// -1.  They are tested before the traversal: neighbouring VPLs are usually
+// hidden by the same triangle.  The answer is the same with or without them
+// (a segment is blocked when any triangle blocks it).
+template <bool COUNT>
+__device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, const Ray &r, int &cache,
+                                              int &cache2, int *stk, int *status, WarpCounters &wc)
+{
+    bool occl = false;
+    if (want && cache >= 0) {
+        if (COUNT) wc.tests++;
+        if (seg_block(r, __ldg(s.tri + 3 * cache), __ldg(s.tri + 3 * cache + 1), __ldg(s.tri + 3 * cache + 2)))
+            occl = true;
+    }
+    if (want && !occl && cache2 >= 0) {
+        if (COUNT) wc.tests++;
+        if (seg_block(r, __ldg(s.tri + 3 * cache2), __ldg(s.tri + 3 * cache2 + 1), __ldg(s.tri + 3 * cache2 + 2))) {
+            occl = true;
+            const int x = cache; cache = cache2; cache2 = x;
+        }
+    }
+    unsigned alive = __ballot_sync(kFull, want && !occl);
+    if (alive == 0) return occl;
+    // Direction signs of the live segments, per axis.  When every live segment
+    // of the packet points the same way along an axis, the entry plane of that
+    // axis is the same box face for all of them, so the packet loads the near
+    // and far rows by address and skips the per-lane min/max that orders the
+    // two plane crossings (the usual case: 32 pixels of a small tile seen from
+    // one VPL).  Otherwise it takes the general slab test.
+    const unsigned nx = __ballot_sync(kFull, want && !occl && signbit(r.inv.x));
+    const unsigned ny = __ballot_sync(kFull, want && !occl && signbit(r.inv.y));
+    const unsigned nz = __ballot_sync(kFull, want && !occl && signbit(r.inv.z));
+    const bool oriented = (nx == 0 || nx == alive) && (ny == 0 || ny == alive) && (nz == 0 || nz == alive);
+    const int fx = nx ? 1 : 0, fy = ny ? 3 : 2, fz = nz ? 5 : 4; // row of each axis' entry plane
+    return oriented ? packet_walk<COUNT, true>(s, want, r, occl, cache, cache2, stk, status, wc, fx, fy, fz)
+                    : packet_walk<COUNT, false>(s, want, r, occl, cache, cache2, stk, status, wc, fx, fy, fz);
 }
 
 template <bool COUNT>
