@@ -4,6 +4,7 @@
 Each test names the passage of the paper (Jin et al., arXiv 2203.11484) it
 pins and what independent fact it uses.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -374,6 +375,72 @@ def test_ir_rejects_close_hits(orc):
     nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
     dist = np.einsum("ij,ij->i", g["pos"][M_c:] - V[T[:, 0]], nrm)
     assert np.abs(dist).max() < 1e-12
+
+
+def _first_bounce_dirs(orc, light, n_paths, seed):
+    """First-bounce VPL positions of n_paths light paths in the closed unit
+    box (every path hits a wall at its first bounce) and their directions
+    from the light's centre."""
+    sc = closed_box_scene(albedo=0.5)
+    sc = dataclasses.replace(sc, light=light)
+    o = orc.OracleScene(sc)
+    cam = _cam(eye=(0.5, 0.5, 0.5), fwd=(1, 0, 0), up=(0, 0, 1))
+    gen = W.GenParams(d_close=0.0, m_close=0, m_far=n_paths, max_bounces=1, seed=seed, ray_eps=1e-6)
+    g = o.generate(cam, gen)
+    assert g["status"] == 0 and g["paths"] == n_paths and (g["tag"] % 16 == 1).all()
+    d = g["pos"] - np.asarray(light.center, np.float64)
+    return g["pos"], d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def _view_factor_corner(X, Y):
+    """View factor from a differential area to a parallel rectangle of sides
+    X, Y (in units of the distance) with the area's normal through one
+    corner (Howell's catalogue, configuration B-3)."""
+    a, b = math.sqrt(1 + X * X), math.sqrt(1 + Y * Y)
+    return (X / a * math.atan(Y / a) + Y / b * math.atan(X / b)) / (2 * math.pi)
+
+
+def test_ir_emission_is_cosine_weighted(orc):
+    """Light paths leave the square light in cosine-weighted directions
+    (Lambertian emitter): with a light too small to matter, E[cos] = 2/3,
+    E[cos^2] = 1/2, the azimuth is uniform, and the share of paths whose
+    first hit is the floor is the view factor from the light's centre to the
+    floor (closed form).  A uniform hemisphere gives E[cos] = 1/2."""
+    n = 40000
+    light = W.Light(center=(0.5, 0.5, 1.0 - 1e-3), normal=(0.0, 0.0, -1.0), edge_u=(1e-4, 0.0, 0.0),
+                    edge_v=(0.0, 1e-4, 0.0), type=W.LIGHT_AREA)
+    pos, d = _first_bounce_dirs(orc, light, n, seed=21)
+    cos = -d[:, 2]
+    se = 1.0 / math.sqrt(n)
+    assert (cos > 0).all()
+    assert abs(cos.mean() - 2 / 3) < 5 * math.sqrt(1 / 18) * se
+    assert abs((cos ** 2).mean() - 0.5) < 5 * math.sqrt(1 / 12) * se
+    for c in (d[:, 0], d[:, 1]):   # E[sin cos phi] = 0, E[sin^2 cos^2 phi] = 1/4
+        assert abs(c.mean()) < 5 * 0.5 * se
+        assert abs((c ** 2).mean() - 0.25) < 5 * 0.25 * se
+    h = 1.0 - 1e-3
+    f_floor = 4 * _view_factor_corner(0.5 / h, 0.5 / h)
+    share = float((pos[:, 2] < 1e-9).mean())
+    assert abs(share - f_floor) < 5 * math.sqrt(f_floor * (1 - f_floor)) * se
+
+
+def test_ir_point_light_emits_uniformly_over_the_sphere(orc):
+    """A point light (type 1, isotropic) at the centre of the closed unit
+    cube: each face subtends 4 pi / 6, so each takes 1/6 of the first hits,
+    and the directions have zero mean with E[d_k^2] = 1/3."""
+    n = 36000
+    light = W.Light(center=(0.5, 0.5, 0.5), normal=(0.0, 0.0, -1.0), edge_u=(0.0, 0.0, 0.0),
+                    edge_v=(0.0, 0.0, 0.0), type=W.LIGHT_POINT)
+    pos, d = _first_bounce_dirs(orc, light, n, seed=22)
+    se = 1.0 / math.sqrt(n)
+    faces = [pos[:, 0] < 1e-9, pos[:, 0] > 1 - 1e-9, pos[:, 1] < 1e-9, pos[:, 1] > 1 - 1e-9,
+             pos[:, 2] < 1e-9, pos[:, 2] > 1 - 1e-9]
+    assert sum(int(f.sum()) for f in faces) == n
+    for f in faces:
+        assert abs(f.mean() - 1 / 6) < 5 * math.sqrt(5 / 36) * se
+    for k in range(3):
+        assert abs(d[:, k].mean()) < 5 * math.sqrt(1 / 3) * se
+        assert abs((d[:, k] ** 2).mean() - 1 / 3) < 5 * math.sqrt(4 / 45) * se
 
 
 # ---------------------------------------------------------------------------
