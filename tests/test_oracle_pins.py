@@ -443,6 +443,38 @@ def test_ir_point_light_emits_uniformly_over_the_sphere(orc):
         assert abs((d[:, k] ** 2).mean() - 1 / 3) < 5 * math.sqrt(4 / 45) * se
 
 
+def test_ir_bounce_directions_are_cosine_weighted_about_the_hit_normal(orc):
+    """Each bounce leaves its hit point in a cosine-weighted direction about
+    the face's normal: between consecutive VPLs of one path in the closed
+    box, E[cos] = 2/3 and E[cos^2] = 1/2 against the first VPL's normal, and
+    the tangent components have zero mean (a frame that favours one tangent
+    direction fails)."""
+    sc = closed_box_scene(albedo=0.5)
+    o = orc.OracleScene(sc)
+    cam = _cam(eye=(0.5, 0.5, 0.5), fwd=(1, 0, 0), up=(0, 0, 1))
+    n = 40000
+    g = o.generate(cam, W.GenParams(d_close=0.0, m_close=0, m_far=2 * n, max_bounces=2, seed=23, ray_eps=1e-6))
+    assert g["status"] == 0 and g["paths"] == n
+    b = g["tag"] % 16
+    first, second = np.flatnonzero(b == 1), np.flatnonzero(b == 2)
+    assert np.array_equal(second, first + 1)
+    d = g["pos"][second] - g["pos"][first]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    nrm = g["nrm"][first]
+    cos = np.einsum("ij,ij->i", d, nrm)
+    se = 1.0 / math.sqrt(n)
+    assert (cos > 0).all()
+    assert abs(cos.mean() - 2 / 3) < 5 * math.sqrt(1 / 18) * se
+    assert abs((cos ** 2).mean() - 0.5) < 5 * math.sqrt(1 / 12) * se
+    # tangent components about each face's normal: the two axes the face spans
+    for axis in range(3):
+        on = np.abs(nrm[:, axis]) > 0.5
+        for t in range(3):
+            if t != axis:
+                c = d[on, t]
+                assert abs(c.mean()) < 5 * 0.5 / math.sqrt(on.sum())
+
+
 # ---------------------------------------------------------------------------
 # gather (Eq. 1 indirect part): closed form of one VPL over a plane, energy
 # ---------------------------------------------------------------------------
