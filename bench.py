@@ -318,7 +318,7 @@ def run_reference(args):
     cam = view.camera
     osc = oracle.OracleScene(wl.scene)
     M = view.gen.m_close + view.gen.m_far
-    n_pix = 64
+    n_pix = 2048
     rng = np.random.default_rng(5)
     for _ in range(args.warmup):
         oracle.render(osc, view, rng.choice(cam.width * cam.height, 8, replace=False))
