@@ -83,3 +83,15 @@ def test_large_render_full_size_crop_parity(large):
     bad = PY.pixel_fail(img[pix], r["image"]) & same
     assert bad.mean() <= 0.03, int(bad.sum())
     assert r["image"].max() > 0
+
+
+def test_large_precision_variants_on_crop(large):
+    """FP32, FP16 attributes + Kahan sums and FP16 plain sums against the
+    FP64 oracle on 1024 receivers of the 256 x 144 crop, 32768 VPLs."""
+    V, ctx, wl, sid, osc = large
+    x0, y0, w, h = wl.crop
+    k = np.random.default_rng(5).choice(w * h, 1024, replace=False)
+    pix = (y0 + k // w) * wl.views[0].camera.width + (x0 + k % w)
+    report = PY.precision_report(V, torch, ctx, sid, osc, wl.views[0], pix, wl.scene.diag())
+    print("precision report, 1M clutter crop (1024 receivers x 32768 VPLs):", report)
+    PY.check_precision_report(report)
