@@ -333,8 +333,12 @@ VPL_API int vpl_debug_rays(vpl_ctx *ctx, vpl_scene_id scene, int32_t mode, int32
                    const float *a, const float *b, int64_t n, int32_t *out_tri, float *out_t,
                    vpl_stream stream);
 /* Visibility bits of the gather for chosen pixels: vis[k * count + i] =
- * 1 visible, 0 blocked, -1 not traced (zero shading term), for pixel
- * pixels[k] (row index) and VPL i.  pixels, vis: device int32 / int8. */
+ * 1 visible, 0 blocked, -1 not traced (zero shading term or zero flux), for
+ * pixel pixels[k] (row index) and VPL i.  pixels, vis: device int32 / int8.
+ * Pixels k * 32 .. k * 32 + 31 of the list form one packet, as the 32
+ * pixels of one tile do in vpl_gather.  A pixel index outside the G-buffer
+ * sets VPL_ERR_INVALID_ARG in the device status (vpl_sync) and its row is
+ * left unwritten. */
 VPL_API int vpl_debug_visibility(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf,
                          const vpl_vpl_set *vpls, const vpl_gather_params *params,
                          const int32_t *pixels, int64_t n_pixels, int8_t *vis,

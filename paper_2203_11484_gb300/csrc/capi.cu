@@ -806,7 +806,7 @@ int vpl_sync(vpl_ctx *ctx, vpl_stream stream)
         const char *what = st == VPL_ERR_TRAVERSAL_LIMIT   ? "a BVH walk hit its step or stack limit"
                            : st == VPL_ERR_EMPTY_CLOSE     ? "no close-range face for m_close > 0"
                            : st == VPL_ERR_PATHS_EXHAUSTED ? "ir_max_paths light paths gave fewer than m_far VPLs"
-                           : st == VPL_ERR_INVALID_ARG     ? "a triangle index was out of range"
+                           : st == VPL_ERR_INVALID_ARG     ? "an index (vertex or debug pixel) was out of range"
                                                            : "device error";
         ctx->err = what;
     }

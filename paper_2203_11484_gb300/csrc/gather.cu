@@ -151,6 +151,11 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
             int64_t q = (int64_t)tile * 32 + lane;
             inb = q < e.n_dbg;
             p = inb ? e.dbg_pixels[q] : 0;
+            if (inb && (p < 0 || p >= (int64_t)width * height)) { // a pixel the image does not have
+                latch(status, VPL_ERR_INVALID_ARG);
+                inb = false;
+                p = 0;
+            }
         } else {
             const int tw = 1 << e.tile_shift, th = 32 >> e.tile_shift;
             const int px = (lt % tiles_x) * tw + (lane & (tw - 1));

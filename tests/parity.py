@@ -183,3 +183,65 @@ def check_precision_report(report: dict) -> None:
         assert report[k]["vs_fp64_fp16_inputs"]["mean_rel"] < 1e-5
     assert (report["fp16_kahan"]["vs_fp64_fp16_inputs"]["mean_rel"]
             <= report["fp16_plain"]["vs_fp64_fp16_inputs"]["mean_rel"] * 1.25 + 1e-9)
+
+
+def explain_render_pixels(V, torch, ctx, sid, osc, view, img, pix, ref_img, same_tri, L_diag):
+    """Pixels of a full-size vpl_render (the benchmark's launch) that are
+    outside the pixel tolerance against the oracle's whole pipeline, each
+    explained.  The render is first checked to equal the G-buffer, the
+    generation and the gather called one by one (bit for bit).  A failing
+    pixel is then recomputed by the oracle's gather from the GPU's own
+    G-buffer row and VPL rows: if it passes, the difference came from the
+    FP32 inputs (bounded by the generation parity tests).  If not, the
+    GPU's visibility bits of that pixel are taken with its whole tile as one
+    packet, exactly as in the render, and the pixel must be explained by
+    flips.  Returns (failing, failing on the GPU's inputs, flips)."""
+    cam = view.camera
+    W_, H_ = cam.width, cam.height
+    gb = V.GBuffer.empty(W_, H_)
+    V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
+    M = view.gen.m_close + view.gen.m_far
+    vs = V.VplSet.empty(M)
+    V.vpl_generate(ctx.h, sid, cam, view.gen, vs)
+    out = torch.zeros((W_ * H_, 4), dtype=torch.float32, device="cuda")
+    V.vpl_gather(ctx.h, sid, gb, vs, view.gather, out)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    assert np.array_equal(out.cpu().numpy()[pix], img[pix])
+    bad = np.asarray(pix)[pixel_fail(img[pix], ref_img) & same_tri]
+    if not len(bad):
+        return 0, 0, 0
+    rows = torch.as_tensor(bad.astype(np.int64)).cuda()
+    gpos = gb.pos[rows].cpu().numpy()
+    g = dict(pos=gpos[:, :3].astype(np.float64), nrm=gb.nrm[rows].cpu().numpy()[:, :3].astype(np.float64),
+             rho=gb.albedo[rows].cpu().numpy()[:, :3].astype(np.float64),
+             tri=gpos[:, 3].copy().view(np.int32).astype(np.int64))
+    v = dict(pos=vs.pos.cpu().numpy()[:, :3].astype(np.float64), nrm=vs.nrm.cpu().numpy()[:, :3].astype(np.float64),
+             flux=vs.flux.cpu().numpy()[:, :3].astype(np.float64))
+    eps = float(np.float32(view.gather.ray_eps))
+    ref2 = osc.gather(g, v, view.gather.d2_min, eps)
+    still = np.nonzero(pixel_fail(img[bad], ref2))[0]
+    if not len(still):
+        return len(bad), 0, 0
+    # each failing pixel's whole 8 x 4 tile, in lane order, as one packet
+    tw, th = 8, 4
+    lists, where = [], {}
+    for k in still:
+        p = int(bad[k])
+        tx, ty = (p % W_) // tw, (p // W_) // th
+        lanes = [(ty * th + l // tw) * W_ + tx * tw + l % tw for l in range(32)]
+        if (tx + 1) * tw > W_ or (ty + 1) * th > H_:
+            lanes = [p] + [p] * 31               # a ragged tile: the pixel alone
+        where[p] = 32 * len(lists) + lanes.index(p)
+        lists.append(lanes)
+    plist = torch.as_tensor(np.asarray(lists, np.int32).reshape(-1)).cuda()
+    vis = torch.zeros((plist.shape[0], M), dtype=torch.int8, device="cuda")
+    V.vpl_debug_visibility(ctx.h, sid, gb, vs, view.gather, plist, vis)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    vis = vis.cpu().numpy()
+    flips = 0
+    for k in still:
+        p = int(bad[k])
+        nf, ok, _ = explain_pixel(osc, g["pos"][k], g["nrm"][k], v, vis[where[p]], view.gather.d2_min, eps, L_diag)
+        assert nf > 0 and ok, (p, img[p], ref2[k], nf)
+        flips += nf
+    return len(bad), len(still), flips

@@ -205,3 +205,28 @@ def test_argument_errors(env):
     assert V.vpl_sync(ctx.h, check=False) == 1
     V.vpl_scene_release(ctx.h, s2)
     assert V.vpl_sync(ctx.h, check=False) == 0       # the status word was cleared
+
+
+def test_debug_visibility_reports_pixels_outside_the_image(env):
+    """A pixel index outside the G-buffer is reported through the device
+    status and its row is left alone; the other rows are written."""
+    V, ctx, wl, sid, _, _ = env
+    view = wl.views[0]
+    cam = view.camera
+    gb = V.GBuffer.empty(cam.width, cam.height)
+    V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
+    M = view.gen.m_close + view.gen.m_far
+    vs = V.VplSet.empty(M)
+    V.vpl_generate(ctx.h, sid, cam, view.gen, vs)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    n_px = cam.width * cam.height
+    pix = torch.tensor([n_px // 2, n_px, -1, n_px // 2 + 1], dtype=torch.int32, device="cuda")
+    vis = torch.full((4, M), 7, dtype=torch.int8, device="cuda")
+    V.vpl_debug_visibility(ctx.h, sid, gb, vs, view.gather, pix, vis)
+    assert V.vpl_sync(ctx.h, check=False) == 1          # VPL_ERR_INVALID_ARG
+    v = vis.cpu().numpy()
+    assert (v[1] == 7).all() and (v[2] == 7).all()      # rows of the bad indices untouched
+    assert np.isin(v[[0, 3]], (-1, 0, 1)).all()
+    # the status word is cleared by the read: the next call starts clean
+    V.vpl_debug_visibility(ctx.h, sid, gb, vs, view.gather, pix[[0, 3]], vis[:2])
+    assert V.vpl_sync(ctx.h, check=False) == 0

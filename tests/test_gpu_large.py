@@ -80,8 +80,10 @@ def test_large_render_full_size_crop_parity(large):
     gtri = gb.pos.cpu().numpy()[pix, 3].copy().view(np.int32)
     same = gtri == r["gbuffer"]["tri"]
     assert same.mean() >= 0.98
-    bad = PY.pixel_fail(img[pix], r["image"]) & same
-    assert bad.mean() <= 0.03, int(bad.sum())
+    M = view.gen.m_close + view.gen.m_far
+    n_bad, n_still, flips = PY.explain_render_pixels(V, torch, ctx, sid, osc, view, img, pix, r["image"], same,
+                                                     wl.scene.diag())
+    assert flips <= max(3, PY.FLIP_FRACTION * len(pix) * M), flips
     assert r["image"].max() > 0
 
 

