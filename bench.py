@@ -197,6 +197,62 @@ def cpu_baseline(workload, seconds: float = 12.0) -> dict:
                       f"value_1core: 256 pixels on one thread"}
 
 
+def cpu_configs(room_pairs_per_s, room_workload) -> dict:
+    """The oracle on the other workloads, each on a bounded sample timed on
+    all host cores (the render of the sampled pixels: their G-buffer, the
+    full VPL generation of the view, the gather): the 64-triangle room in
+    full frame, two views of the 64-view batch (1024 sampled pixels each),
+    1024 pixels of the 1M clutter's 256 x 144 crop.  Times beyond a sample
+    (the full frame, the crop, all 64 views) are extrapolated from its
+    pairs/s and marked so."""
+    import oracle
+    from paper_2203_11484_gb300 import workloads as W
+    rng = np.random.default_rng(78)
+    out = {}
+    v0 = room_workload.views[0]
+    room_pairs = v0.camera.width * v0.camera.height * (v0.gen.m_close + v0.gen.m_far)
+    out["room200k"] = {"workload": room_workload.name, "pairs_per_s": room_pairs_per_s,
+                       "sample": "the cpu_baseline sample", "full_frame_s": room_pairs / room_pairs_per_s,
+                       "extrapolated": True}
+    wl = W.cornell_workload()
+    v = wl.views[0]
+    osc = oracle.OracleScene(wl.scene)
+    pairs = v.camera.width * v.camera.height * (v.gen.m_close + v.gen.m_far)
+    t0 = time.perf_counter()
+    oracle.render(osc, v)
+    dt = time.perf_counter() - t0
+    out["cornell"] = {"workload": wl.name, "pairs_per_s": pairs / dt, "sample": "full frame, brute-force visibility",
+                      "full_frame_s": dt, "extrapolated": False}
+    wl = W.batch_views()
+    osc = oracle.OracleScene(wl.scene)
+    pairs, dt = 0, 0.0
+    for v in wl.views[:2]:
+        M = v.gen.m_close + v.gen.m_far
+        pix = rng.choice(v.camera.width * v.camera.height, 1024, replace=False)
+        t0 = time.perf_counter()
+        oracle.render(osc, v, pix)
+        dt += time.perf_counter() - t0
+        pairs += 1024 * M
+    all_pairs = sum(v.camera.width * v.camera.height * (v.gen.m_close + v.gen.m_far) for v in wl.views)
+    out["batch"] = {"workload": wl.name, "pairs_per_s": pairs / dt, "sample": "2 views x 1024 sampled pixels",
+                    "full_frame_s": all_pairs / (pairs / dt), "extrapolated": True}
+    wl = W.room1m_workload()
+    v = wl.views[0]
+    osc = oracle.OracleScene(wl.scene)
+    M = v.gen.m_close + v.gen.m_far
+    x0, y0, w, h = wl.crop
+    k = rng.choice(w * h, 1024, replace=False)
+    pix = (y0 + k // w) * v.camera.width + (x0 + k % w)
+    t0 = time.perf_counter()
+    oracle.render(osc, v, pix)
+    dt = time.perf_counter() - t0
+    rate = 1024 * M / dt
+    out["clutter1m"] = {"workload": wl.name, "pairs_per_s": rate, "sample": "1024 pixels of the 256 x 144 crop",
+                        "crop_s": w * h * M / rate, "full_frame_s": v.camera.width * v.camera.height * M / rate,
+                        "extrapolated": True}
+    return out
+
+
 def batch_section(ctx, n_views: int, precision: int, reps: int = 2) -> dict:
     """Many close-up views of the resident 200k-triangle room with uneven
     resolutions and VPL budgets: one vpl_render per view (one launch sequence
@@ -559,6 +615,8 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         try:
             cpu = cpu_baseline(wl, seconds=args.cpu_seconds)
+            if args.workload == "room200k" and args.width == 0 and args.height == 0 and args.vpls == 0:
+                cpu["configs"] = cpu_configs(cpu["value"], wl)
         except Exception as exc:  # the baseline is reported, never required
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
 
