@@ -499,6 +499,8 @@ __device__ __forceinline__ bool packet_walk(const SceneView &s, bool want, const
     // parameter is huge, so their slab tests fail without a predicate
     unsigned long long kx2 = cx2, ky2 = cy2, kz2 = cz2;
     if (!(want && !occl)) kx2 = ky2 = kz2 = pack2(3.0e38f, 3.0e38f);
+    // the entry-plane row of each axis, as an address from which each node's row follows
+    const float4 *bx = s.nodes + fx, *by = s.nodes + fy, *bz = s.nodes + fz;
     int sp = 0, node = 0, steps = 0;
     while (true) {
         Node4 n;
@@ -506,10 +508,15 @@ __device__ __forceinline__ bool packet_walk(const SceneView &s, bool want, const
         unsigned hits = 0;     // children this lane's segment enters
         if (ORIENTED) {
             const float4 *p = s.nodes + 8 * (int64_t)node;
+            // entry rows from the walk's per-axis bases; each exit row is the
+            // other row of its 32-byte pair (node rows are 128-byte aligned)
+            const float4 *pex = bx + 8 * (int64_t)node, *pey = by + 8 * (int64_t)node, *pez = bz + 8 * (int64_t)node;
+            const float4 *pxx = (const float4 *)((uintptr_t)pex ^ 16u), *pxy = (const float4 *)((uintptr_t)pey ^ 16u),
+                         *pxz = (const float4 *)((uintptr_t)pez ^ 16u);
             // plane crossings of all four children, two per instruction
-            const float4 ex = fma4(__ldg(p + fx), sx2, kx2), xx = fma4(__ldg(p + (fx ^ 1)), sx2, kx2);
-            const float4 ey = fma4(__ldg(p + fy), sy2, ky2), xy = fma4(__ldg(p + (fy ^ 1)), sy2, ky2);
-            const float4 ez = fma4(__ldg(p + fz), sz2, kz2), xz = fma4(__ldg(p + (fz ^ 1)), sz2, kz2);
+            const float4 ex = fma4(__ldg(pex), sx2, kx2), xx = fma4(__ldg(pxx), sx2, kx2);
+            const float4 ey = fma4(__ldg(pey), sy2, ky2), xy = fma4(__ldg(pxy), sy2, ky2);
+            const float4 ez = fma4(__ldg(pez), sz2, kz2), xz = fma4(__ldg(pxz), sz2, kz2);
             load_node4_meta(p, n);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
