@@ -275,7 +275,10 @@ VPL_API int vpl_gather(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf
  * Each call clears the counter before its launch; all calls share the array,
  * so calls that overlap on the GPU (other streams, other contexts on the same
  * device) race on it and must be ordered by the caller.  Images of more than
- * 2^30 tiles of 8 x 4 pixels return VPL_ERR_INVALID_ARG. */
+ * 2^30 tiles of 32 pixels in the tile shape of params->tile_w return
+ * VPL_ERR_INVALID_ARG.  The looked-up address is kept for the life of the
+ * process: after the application resets a device (cudaDeviceReset), this
+ * entry point must not be called on that device again. */
 VPL_API int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf,
                                const vpl_vpl_set *vpls, const vpl_gather_params *params,
                                float *out_rgba, vpl_stream stream);
@@ -350,6 +353,13 @@ VPL_API int vpl_set_timing(vpl_ctx *ctx, int32_t on);
 VPL_API int vpl_stage_times(vpl_ctx *ctx, float *ms, int32_t n);
 /* Kernel launches enqueued by this context since its creation. */
 VPL_API int64_t vpl_launch_count(const vpl_ctx *ctx);
+/* Bytes of the context's stream-ordered pool (the library's temporaries):
+ * out[0] in use now, out[1] the most in use at once since the context was
+ * created or since the last call with reset_high != 0 (which first sets the
+ * mark to the bytes in use now), out[2] reserved from the device.  Host-side
+ * query; it waits for nothing, so synchronise the streams whose calls should
+ * be counted first.  Not in the paper: a diagnostic of memory admission. */
+VPL_API int vpl_pool_stats(vpl_ctx *ctx, int32_t reset_high, uint64_t out[3]);
 /* Work counters of one gather launch (not timed): out[0] pairs with a
  * non-empty receiver, [1] pairs with a non-zero shading term (shadow rays),
  * [2] BVH node visits summed over rays, [3] triangle tests summed over rays,

@@ -104,6 +104,10 @@ def lib() -> C.CDLL:
             L.orc_generate_rs.restype = C.c_int64
             L.orc_light_vpls.argtypes = [C.POINTER(_Light), C.c_int64, C.c_uint64, _D, _D, _D, _I64]
             L.orc_light_vpls.restype = C.c_int64
+            L.orc_close_order.argtypes = [_P, _U8, _I64]
+            L.orc_close_order.restype = C.c_int64
+            L.orc_ir_path.argtypes = [_P, C.POINTER(_Light), C.POINTER(_Gen), C.c_int64, _D, _D, _I64, _D, _I64]
+            L.orc_ir_path.restype = C.c_int64
             L.orc_num_threads.restype = C.c_int32
             L.orc_set_threads.argtypes = [C.c_int32]
             _lib = L
@@ -238,6 +242,28 @@ class OracleScene:
         lib().orc_classify(self.h, C.byref(c), C.byref(self.light), float(d_close), int(rule),
                            _ptr(flags, C.c_uint8))
         return flags.astype(bool)
+
+    def close_order(self, mask) -> np.ndarray:
+        """Triangle indices of the faces with mask != 0 in the order the
+        patch sampling walks them (orc_close_order)."""
+        m = np.ascontiguousarray(np.asarray(mask, dtype=bool).astype(np.uint8))
+        assert m.shape == (self.scene.n_tris,)
+        out = np.zeros(max(int(m.sum()), 1), np.int64)
+        n = lib().orc_close_order(self.h, _ptr(m, C.c_uint8), _ptr(out, C.c_int64))
+        return out[:n]
+
+    def ir_path(self, gen, p: int, vis_mode=0) -> dict:
+        """The rays of instant-radiosity light path p (orc_ir_path): origin,
+        direction, triangle hit (-1 miss), t and whether it was a front-face
+        hit, one row per ray cast."""
+        B = max(int(gen.max_bounces), 1)
+        o, d, t = np.zeros((B, 3)), np.zeros((B, 3)), np.zeros(B)
+        k, front = np.zeros(B, np.int64), np.zeros(B, np.int64)
+        g = gen_struct(gen, vis_mode)
+        n = lib().orc_ir_path(self.h, C.byref(self.light), C.byref(g), int(p), _ptr(o, C.c_double),
+                              _ptr(d, C.c_double), _ptr(k, C.c_int64), _ptr(t, C.c_double),
+                              _ptr(front, C.c_int64))
+        return dict(o=o[:n], d=d[:n], k=k[:n], t=t[:n], front=front[:n].astype(bool))
 
     def generate(self, cam, gen, vis_mode=0) -> dict:
         M = int(gen.m_close) + int(gen.m_far)

@@ -600,6 +600,80 @@ static d3 sphere_dir(double s1, double s2)
 }
 
 /* ------------------------------------------------------------------------ */
+/* one instant-radiosity light path (pipeline step (3)): the rays it casts    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    d3 o, d;       /* ray origin and direction                               */
+    int64_t k;     /* triangle hit (closest, t > 0), -1 on a miss            */
+    double t;      /* its ray parameter                                      */
+    int front;     /* 1: front face hit, x is a path vertex; 0: the path ends */
+    d3 x;          /* hit point o + t d (front hits)                         */
+} irray;
+
+/* Path p: start on the light (Philox key (seed, STREAM_IR), counter (p, 0):
+ * words w0, w1 the point, w2, w3 the direction; cosine-weighted about the
+ * light's normal, or uniform on the sphere for a point light), then at most
+ * max_bounces closest hits; after each front-face hit x on face k the next
+ * direction is cosine-weighted about n_k with counter (p, b) and the next
+ * ray starts at x + ray_eps n_k.  A miss or a back-face hit (one-sided faces
+ * absorb from behind) ends the path.  Writes the rays cast, returns how many. */
+static int ir_path(const oscene *s, const olight *L, const ogen *G, int64_t p, irray *out)
+{
+    uint64_t w[4];
+    rng4(G->seed, STREAM_IR, (uint64_t)p, 0, w);
+    d3 o, d;
+    if (L->type == 1) {
+        o = ld3(L->center);
+        d = sphere_dir(u01(w[2]), u01(w[3]));
+    } else {
+        o = light_point(L, u01(w[0]), u01(w[1]));
+        d = cosine_dir(ld3(L->normal), u01(w[2]), u01(w[3]));
+    }
+    int n = 0;
+    for (int32_t b = 1; b <= G->max_bounces; b++) {
+        double t;
+        int64_t k = closest(s, o, d, 0.0, &t, G->vis_mode);
+        irray *r = &out[n++];
+        r->o = o;
+        r->d = d;
+        r->k = k;
+        r->t = t;
+        r->front = 0;
+        r->x = mk(0, 0, 0);
+        if (k < 0) break;
+        if (!(dot(d, s->cr[k]) < 0.0)) break;   /* back face absorbs */
+        d3 x = add(o, scl(d, t));
+        r->front = 1;
+        r->x = x;
+        if (b == G->max_bounces) break;
+        rng4(G->seed, STREAM_IR, (uint64_t)p, (uint64_t)b, w);
+        d = cosine_dir(s->n[k], u01(w[0]), u01(w[1]));
+        o = add(x, scl(s->n[k], G->ray_eps));
+    }
+    return n;
+}
+
+/* The rays of light path p (ir_path) for replay by the tests: per ray its
+ * origin o[3i..], direction d[3i..], triangle k[i] (-1 miss), t[i] and
+ * front[i]; arrays of max_bounces entries.  Returns the number of rays. */
+ORC_API int64_t orc_ir_path(void *sp, const olight *L, const ogen *G, int64_t p, double *o, double *d,
+                            int64_t *k, double *t, int64_t *front)
+{
+    const oscene *s = (const oscene *)sp;
+    irray *r = malloc(sizeof(irray) * (size_t)(G->max_bounces > 0 ? G->max_bounces : 1));
+    int n = ir_path(s, L, G, p, r);
+    for (int i = 0; i < n; i++) {
+        st3(o + 3 * i, r[i].o);
+        st3(d + 3 * i, r[i].d);
+        k[i] = r[i].k;
+        t[i] = r[i].t;
+        front[i] = r[i].front;
+    }
+    free(r);
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
 /* VPL generation (pipeline steps (1)-(3))                                  */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -618,6 +692,41 @@ static int cmp_mkey(const void *pa, const void *pb)
     const mkey *a = (const mkey *)pa, *b = (const mkey *)pb;
     if (a->code != b->code) return a->code < b->code ? -1 : 1;
     return a->tri < b->tri ? -1 : (a->tri > b->tri);
+}
+
+/* Spatial order of the close-range faces ("Realization": the faces are
+ * sorted by the Morton code of their position): the FP64 centroid of each
+ * face with mask[t] != 0, normalised into the AABB of the centroids of ALL
+ * faces, quantised to 21 bits per axis (quant21), interleaved (orc_morton63)
+ * and sorted ascending by (code, triangle index).  keys gets nc entries. */
+static void close_order(const oscene *s, const uint8_t *mask, int64_t nc, mkey *keys)
+{
+    int64_t j = 0;
+    for (int64_t t = 0; t < s->nt && j < nc; t++) {
+        if (!mask[t]) continue;
+        d3 g = s->g[t];
+        keys[j].code = orc_morton63(quant21(g.x, s->glo.x, s->ghi.x),
+                                    quant21(g.y, s->glo.y, s->ghi.y),
+                                    quant21(g.z, s->glo.z, s->ghi.z));
+        keys[j].tri = (int32_t)t;
+        j++;
+    }
+    qsort(keys, (size_t)nc, sizeof(mkey), cmp_mkey);
+}
+
+/* The order close_order gives the faces with mask[t] != 0 (their triangle
+ * indices into out, which holds one entry per set mask byte); returns how
+ * many.  The patch sampling of orc_generate walks its strata in this order. */
+ORC_API int64_t orc_close_order(void *sp, const uint8_t *mask, int64_t *out)
+{
+    const oscene *s = (const oscene *)sp;
+    int64_t nc = 0;
+    for (int64_t t = 0; t < s->nt; t++) nc += mask[t] != 0;
+    mkey *keys = malloc(sizeof(mkey) * (size_t)(nc > 0 ? nc : 1));
+    close_order(s, mask, nc, keys);
+    for (int64_t i = 0; i < nc; i++) out[i] = keys[i].tri;
+    free(keys);
+    return nc;
 }
 
 /* Eq. 2 for a VPL at x (unit normal n, albedo rho, area D): reflected power */
@@ -677,17 +786,7 @@ ORC_API int64_t orc_generate(void *sp, const ocamera *cam, const olight *L, cons
             /* spatial order: Morton code of the centroid in the AABB of all
              * centroids, ties by triangle index */
             mkey *keys = malloc(sizeof(mkey) * nc);
-            int64_t j = 0;
-            for (int64_t t = 0; t < s->nt; t++) {
-                if (!close[t]) continue;
-                d3 g = s->g[t];
-                keys[j].code = orc_morton63(quant21(g.x, s->glo.x, s->ghi.x),
-                                            quant21(g.y, s->glo.y, s->ghi.y),
-                                            quant21(g.z, s->glo.z, s->ghi.z));
-                keys[j].tri = (int32_t)t;
-                j++;
-            }
-            qsort(keys, (size_t)nc, sizeof(mkey), cmp_mkey);
+            close_order(s, close, nc, keys);
             /* integer areas q_t = round(A_t 2^S) with S = 40 - exponent(max A) */
             double amax = 0.0;
             for (int64_t i = 0; i < nc; i++) amax = dmax(amax, s->area[keys[i].tri]);
@@ -781,30 +880,19 @@ ORC_API int64_t orc_generate(void *sp, const ocamera *cam, const olight *L, cons
     if (G->m_far > 0) {
         const int64_t base = G->m_close;
         int64_t kept = 0, p = 0, P = 0;
-        d3 nl = ld3(L->normal);
         const int64_t pmax = G->ir_max_paths;
+        irray *rays = malloc(sizeof(irray) * (size_t)(G->max_bounces > 0 ? G->max_bounces : 1));
         while (kept < G->m_far && p < pmax) {
-            uint64_t w[4];
-            rng4(G->seed, STREAM_IR, (uint64_t)p, 0, w);
-            d3 o, d;
-            if (L->type == 1) {
-                o = ld3(L->center);
-                d = sphere_dir(u01(w[2]), u01(w[3]));
-            } else {
-                o = light_point(L, u01(w[0]), u01(w[1]));
-                d = cosine_dir(nl, u01(w[2]), u01(w[3]));
-            }
+            int n = ir_path(s, L, G, p, rays);
             double thr[3] = {1.0, 1.0, 1.0};
-            for (int32_t b = 1; b <= G->max_bounces && kept < G->m_far; b++) {
-                double t;
-                int64_t k = closest(s, o, d, 0.0, &t, G->vis_mode);
-                if (k < 0) break;
-                if (!(dot(d, s->cr[k]) < 0.0)) break;   /* back face absorbs */
-                d3 x = add(o, scl(d, t));
+            for (int32_t b = 1; b <= n && kept < G->m_far; b++) {
+                const irray *r = &rays[b - 1];
+                if (!r->front) break;
+                int64_t k = r->k;
                 for (int c = 0; c < 3; c++) thr[c] = thr[c] * s->rho[3 * k + c];
                 if (!close[k]) {
                     int64_t i = base + kept;
-                    st3(pos + 3 * i, x);
+                    st3(pos + 3 * i, r->x);
                     st3(nrm + 3 * i, s->n[k]);
                     st3(flux + 3 * i, mk(thr[0], thr[1], thr[2]));
                     tri[i] = k;
@@ -812,13 +900,10 @@ ORC_API int64_t orc_generate(void *sp, const ocamera *cam, const olight *L, cons
                     kept++;
                     P = p + 1;
                 }
-                if (b == G->max_bounces) break;
-                rng4(G->seed, STREAM_IR, (uint64_t)p, (uint64_t)b, w);
-                d = cosine_dir(s->n[k], u01(w[0]), u01(w[1]));
-                o = add(x, scl(s->n[k], G->ray_eps));
             }
             p++;
         }
+        free(rays);
         if (kept < G->m_far) { info->status = 7; P = pmax; }
         info->paths = P;
         info->m_far_kept = kept;
@@ -939,37 +1024,24 @@ ORC_API int64_t orc_generate_rs(void *sp, const ocamera *cam, const olight *L, c
     int64_t *ck = malloc(sizeof(int64_t) * (size_t)(ns > 0 ? ns : 1));
     double *cc = calloc((size_t)(ns > 0 ? ns : 1), sizeof(double));
     for (int64_t i = 0; i < ns; i++) ck[i] = -1;
-    d3 nl = ld3(L->normal);
     #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t p = 0; p < pmax; p++) {
-        uint64_t w[4];
-        rng4(G->seed, STREAM_IR, (uint64_t)p, 0, w);
-        d3 o, d;
-        if (L->type == 1) {
-            o = ld3(L->center);
-            d = sphere_dir(u01(w[2]), u01(w[3]));
-        } else {
-            o = light_point(L, u01(w[0]), u01(w[1]));
-            d = cosine_dir(nl, u01(w[2]), u01(w[3]));
-        }
+        irray rays[64];
+        irray *rp = B <= 64 ? rays : malloc(sizeof(irray) * (size_t)B);
+        int n = ir_path(s, L, G, p, rp);
         double thr[3] = {1.0, 1.0, 1.0};
-        for (int64_t b = 1; b <= B; b++) {
-            double t;
-            int64_t k = closest(s, o, d, 0.0, &t, G->vis_mode);
-            if (k < 0) break;
-            if (!(dot(d, s->cr[k]) < 0.0)) break;   /* back face absorbs */
-            d3 x = add(o, scl(d, t));
+        for (int64_t b = 1; b <= n; b++) {
+            const irray *r = &rp[b - 1];
+            if (!r->front) break;
+            int64_t k = r->k;
             for (int c = 0; c < 3; c++) thr[c] = thr[c] * s->rho[3 * k + c];
             int64_t slot = p * B + (b - 1);
-            cx[slot] = x;
+            cx[slot] = r->x;
             cn[slot] = s->n[k];
             for (int c = 0; c < 3; c++) ct[3 * slot + c] = thr[c];
             ck[slot] = k;
-            if (b == B) break;
-            rng4(G->seed, STREAM_IR, (uint64_t)p, (uint64_t)b, w);
-            d = cosine_dir(s->n[k], u01(w[0]), u01(w[1]));
-            o = add(x, scl(s->n[k], G->ray_eps));
         }
+        if (rp != rays) free(rp);
     }
     /* pilot pixels: a pilot x ph grid over the same view */
     const int64_t pw = pilot, ph0 = ((int64_t)pilot * cam->height + cam->width / 2) / cam->width;

@@ -581,11 +581,15 @@ int vpl_gather_noalloc(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf
     const int64_t tiles = (((int64_t)gbuf->width + tw - 1) / tw) * (((int64_t)gbuf->height + th - 1) / th);
     if (tiles > gather_noalloc_max_tiles())
         return fail(ctx, VPL_ERR_INVALID_ARG,
-                    "vpl_gather_noalloc: image has more than 2^30 tiles of 8x4 pixels, the most its static "
-                    "tile counter supports");
+                    "vpl_gather_noalloc: image has more than 2^30 tiles of 32 pixels in the chosen tile shape, "
+                    "the most its static tile counter supports");
     DeviceGuard g(ctx->device);
     Exec ex = exec_of(ctx, stream);
+    // timed like vpl_gather (the events are created with the context)
+    for (int k = 2; k < 4; k++) ctx->ev_valid[k] = false;
+    mark(ctx, 4, stream);
     CK(ctx, gather_noalloc(ex, view_of(s), gather_args(gbuf, vpls, params, out_rgba)), "vpl_gather_noalloc");
+    mark(ctx, 5, stream);
     return VPL_OK;
 }
 
@@ -882,6 +886,24 @@ int vpl_stage_times(vpl_ctx *ctx, float *ms, int32_t n)
 }
 
 int64_t vpl_launch_count(const vpl_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int vpl_pool_stats(vpl_ctx *ctx, int32_t reset_high, uint64_t out[3])
+{
+    if (!ctx || !out) return VPL_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    unsigned long long used = 0, high = 0, reserved = 0;
+    if (reset_high) {
+        unsigned long long zero = 0;
+        CK(ctx, cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &zero), "vpl_pool_stats");
+    }
+    CK(ctx, cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &used), "vpl_pool_stats");
+    CK(ctx, cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &high), "vpl_pool_stats");
+    CK(ctx, cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrReservedMemCurrent, &reserved), "vpl_pool_stats");
+    out[0] = used;
+    out[1] = high;
+    out[2] = reserved;
+    return VPL_OK;
+}
 
 int vpl_gather_counters(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf, const vpl_vpl_set *vpls,
                         const vpl_gather_params *params, uint64_t out[6], vpl_stream stream)

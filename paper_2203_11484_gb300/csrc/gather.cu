@@ -7,8 +7,10 @@
 // lanes, so the 32 shadow segments of one step all end at the same VPL and
 // start from neighbouring pixels: the warp traverses the BVH as one packet
 // (warp_occluded).  Tiles are handed out dynamically (an atomic counter) to a
-// grid of resident blocks.  Each pixel sums its VPLs in index order in one
-// thread, so the result does not depend on tiling or batching.
+// grid of resident blocks.  Each pixel sums its VPLs in one thread, in the
+// order of the permutation v_order (the Morton order of the VPL positions
+// that the gather entry points sort; the given order when there is none), so
+// the result does not depend on tiling or batching.
 #include <mutex>
 
 #include "vpl_internal.h"

@@ -115,6 +115,7 @@ _SIGS = {
     "vpl_set_timing": (C.c_int, [_P, C.c_int32]),
     "vpl_stage_times": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int32]),
     "vpl_launch_count": (C.c_int64, [_P]),
+    "vpl_pool_stats": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_uint64)]),
     "vpl_gather_counters": (C.c_int, [_P, C.c_uint64, C.POINTER(vpl_gbuffer), C.POINTER(vpl_vpl_set),
                                       C.POINTER(vpl_gather_params), C.POINTER(C.c_uint64), _P]),
 }
@@ -427,6 +428,12 @@ def vpl_stage_times(ctx) -> list:
 
 def vpl_launch_count(ctx) -> int:
     return int(load().vpl_launch_count(ctx))
+
+
+def vpl_pool_stats(ctx, reset_high: bool = False) -> dict:
+    out = (C.c_uint64 * 3)()
+    _check(ctx, load().vpl_pool_stats(ctx, 1 if reset_high else 0, out), "vpl_pool_stats")
+    return dict(used=int(out[0]), high=int(out[1]), reserved=int(out[2]))
 
 
 def vpl_gather_counters(ctx, scene: int, gbuf: GBuffer, vpls: VplSet, params: W.GatherParams,

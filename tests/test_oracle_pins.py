@@ -87,6 +87,123 @@ def test_morton_bit_interleave(orc):
         assert back == q
 
 
+def _morton_order_restated(verts, tris, mask, aabb="all", axes=(0, 1, 2), bits=21, ties=1):
+    """The order of the close faces restated from Sec. 3 "Realization" (sort
+    the faces by the Morton code of their position) and the reading that
+    fixes its details: FP64 centroids ((a + b) + c) / 3 of the FP32
+    vertices, normalised into the AABB of the centroids of ALL faces,
+    floor(t 2^21) clamped to [0, 2^21 - 1] per axis, bit i of x, y, z at bit
+    3i + 2, 3i + 1, 3i, and Python's sorted() on (code, index).  The keyword
+    arguments plant the plausible slips the pin must catch (another box,
+    swapped axes, another resolution, ties the other way)."""
+    V = np.asarray(verts, np.float32).astype(np.float64)
+    T = np.asarray(tris)
+    g = ((V[T[:, 0]] + V[T[:, 1]]) + V[T[:, 2]]) / 3.0
+    sel = np.nonzero(mask)[0]
+    if aabb == "all":
+        lo, hi = g.min(axis=0), g.max(axis=0)
+    elif aabb == "close":
+        lo, hi = g[sel].min(axis=0), g[sel].max(axis=0)
+    else:  # the vertex box
+        lo, hi = V[T.reshape(-1)].min(axis=0), V[T.reshape(-1)].max(axis=0)
+    keys = []
+    for t in sel:
+        code = 0
+        for slot, a in enumerate(axes):
+            u = (g[t, a] - lo[a]) / (hi[a] - lo[a]) if hi[a] > lo[a] else 0.0
+            q = min(max(math.floor(u * 2 ** bits), 0), 2 ** bits - 1)
+            for bit in range(bits):
+                code |= ((q >> bit) & 1) << (3 * bit + 2 - slot)
+        keys.append((code, ties * int(t)))
+    return [ties * t for _, t in sorted(keys)]
+
+
+def _morton_pin_scene():
+    """Faces whose centroids span very unequal extents (x 100, y 2, z 0.02,
+    negative coordinates included), a few long faces that reach far beyond
+    the centroid box (so the vertex box differs), exact duplicates (equal
+    codes) and pairs closer than one quantisation cell (equal codes, unequal
+    centroids); the faces that set the centroid box are left out of the
+    mask, so the box of the masked centroids differs too."""
+    rng = np.random.default_rng(21)
+    cents = np.stack([rng.uniform(-50, 50, 400), rng.uniform(0, 2, 400), rng.uniform(-0.01, 0.01, 400)], 1)
+    tv = []
+    for c in cents:
+        d1, d2 = rng.normal(0, 0.05, 3), rng.normal(0, 0.05, 3)
+        tv.append([c + d1, c + d2, c - d1 - d2])
+    for k in range(6):                      # long faces: vertices out to |x| = 300
+        c = cents[k]
+        tv.append([c + (250.0, 0, 0), c - (250.0, 0, 0), c + (0, 0.01, 0)])
+    for k in range(20):                     # duplicates of faces 10..29
+        tv.append([v.copy() for v in tv[10 + k]])
+    for k in range(20):                     # 1e-9 of the box apart from faces 40..59
+        tv.append([v + (1e-7, 0, 0) for v in tv[40 + k]])
+    cell = 100.0 / 2 ** 21
+    for k in range(20):                     # one 21-bit cell below faces 70..89 in x
+        tv.append([v - (cell, 0, 0) for v in tv[70 + k]])
+    verts = np.array([p for t in tv for p in t], np.float32)
+    tris = np.arange(len(verts)).reshape(-1, 3)
+    V = verts.astype(np.float64)
+    g = ((V[tris[:, 0]] + V[tris[:, 1]]) + V[tris[:, 2]]) / 3.0
+    mask = rng.random(len(tris)) < 0.7
+    mask[10:30] = mask[400 + 6:400 + 26] = True
+    mask[40:60] = mask[426:446] = True
+    mask[70:90] = mask[446:466] = True
+    for a in range(3):                      # the faces that set the centroid box
+        mask[np.argmin(g[:, a])] = mask[np.argmax(g[:, a])] = False
+    return tri_scene(verts, tris, 0.5), mask
+
+
+def test_morton_close_order_restated(orc):
+    """The order the patch sampling walks (orc_close_order) equals the
+    restatement, and each planted slip gives another order, so the pin
+    would see it."""
+    sc, mask = _morton_pin_scene()
+    o = orc.OracleScene(sc)
+    got = o.close_order(mask).tolist()
+    want = _morton_order_restated(sc.verts, sc.tris, mask)
+    assert got == want
+    assert len(got) == int(mask.sum())
+    for slip in (dict(aabb="close"), dict(aabb="verts"), dict(axes=(2, 1, 0)), dict(axes=(1, 0, 2)),
+                 dict(bits=20), dict(ties=-1)):
+        assert _morton_order_restated(sc.verts, sc.tris, mask, **slip) != want, slip
+    assert sorted(got) != got                # not the index order either
+    # equal codes are ordered by index: a duplicate, and a copy less than one
+    # cell away, directly follow their original; a copy one cell lower in x
+    # comes first
+    pos = {t: i for i, t in enumerate(got)}
+    both = lambda a, b: a in pos and b in pos
+    pairs = [(10 + k, 406 + k) for k in range(20)] + [(40 + k, 426 + k) for k in range(20)]
+    assert sum(both(a, b) for a, b in pairs) >= 36
+    for a, b in pairs:
+        assert not both(a, b) or pos[b] == pos[a] + 1, (a, b)
+    below = [(70 + k, 446 + k) for k in range(20) if both(70 + k, 446 + k)]
+    assert len(below) >= 18 and sum(pos[b] < pos[a] for a, b in below) >= len(below) - 1
+
+
+@pytest.mark.parametrize("which", ["cornell", "room"])
+def test_patch_strata_follow_the_morton_order(orc, which):
+    """orc_generate assigns strata along that order: the faces of consecutive
+    patch VPLs are non-decreasing in the restated order, and with many VPLs
+    every close face with a large enough area is reached."""
+    wl = W.cornell_workload() if which == "cornell" else W.room200k_workload()
+    v = wl.views[0]
+    o = orc.OracleScene(wl.scene)
+    close = o.classify(v.camera, v.gen.d_close)
+    order = _morton_order_restated(wl.scene.verts, wl.scene.tris, close)
+    assert o.close_order(close).tolist() == order
+    K = 4000 if which == "cornell" else 20000
+    gen = dataclasses.replace(v.gen, m_close=K, m_far=0)
+    g = o.generate(v.camera, gen, vis_mode=1 if which == "cornell" else 0)
+    rank = {t: i for i, t in enumerate(order)}
+    r = np.array([rank[int(t)] for t in g["tri"]])
+    assert (np.diff(r) >= 0).all()
+    A = _areas(wl.scene)
+    big = [t for t in order if A[t] * K > 2 * A[close].sum()]   # >= 2 strata wide: reached
+    assert set(big) <= set(g["tri"].tolist())
+    assert len(big) >= min(8, len(order))
+
+
 # ---------------------------------------------------------------------------
 # close/distant split (Sec. 3): one-sided, in the field of view, nearer than a
 # threshold; patch sampling only on faces facing the light
@@ -821,3 +938,20 @@ def test_rs_keeps_only_vpls_that_light_the_pilot_pixels(orc):
     for k in range(len(rs["pos"])):
         one = dict(pos=rs["pos"][k:k + 1], nrm=rs["nrm"][k:k + 1], flux=np.ones((1, 3)))
         assert o.gather(gb, one, v.gather.d2_min, v.gather.ray_eps, vis_mode=1).sum() > 0, k
+
+
+def test_ir_path_replay_matches_generation(orc):
+    """orc_ir_path (the replay the GPU parity tests use to explain a light
+    path that changed course) gives the rays of orc_generate's walks: each
+    far VPL tagged (p, b) is the front hit of ray b of path p, at o + t d."""
+    wl = W.room200k_workload()
+    v = wl.views[0]
+    o = orc.OracleScene(wl.scene)
+    g = o.generate(v.camera, v.gen, vis_mode=0)
+    Mc = v.gen.m_close
+    for i in range(Mc, Mc + v.gen.m_far, 7):
+        p, b = divmod(int(g["tag"][i]), 16)
+        r = o.ir_path(v.gen, p)
+        assert len(r["k"]) >= b and r["front"][b - 1] and r["k"][b - 1] == g["tri"][i]
+        assert np.array_equal(r["o"][b - 1] + r["d"][b - 1] * r["t"][b - 1], g["pos"][i])
+        assert (r["front"][:b]).all()

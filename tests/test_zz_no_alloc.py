@@ -85,4 +85,32 @@ def test_noalloc_gather_rejects_oversized_image(setup):
     import ctypes as C
     rc = V.load().vpl_gather_noalloc(ctx.h, sid, C.byref(gb), C.byref(vs), C.byref(p), 256, None)
     assert rc == 1
-    assert "2^30 tiles" in V.vpl_last_error(ctx.h)
+    assert "2^30 tiles of 32 pixels" in V.vpl_last_error(ctx.h)
+
+
+def test_noalloc_gather_allocates_nothing(setup):
+    """What the entry point is for: a call takes no memory from the
+    library's pool and none from the device.  vpl_gather on the same inputs
+    does draw on the pool (tile counter, VPL sort), which shows the check can
+    see an allocation."""
+    V, ctx, wl, sid = setup
+    view = wl.views[0]
+    gb, vs = _inputs(V, ctx, sid, view, 128, 128)
+    out = torch.zeros((128 * 128, 4), dtype=torch.float32, device="cuda")
+    V.vpl_gather_noalloc(ctx.h, sid, gb, vs, view.gather, out)   # first call: address look-up
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    torch.cuda.synchronize()
+    before = V.vpl_pool_stats(ctx.h, reset_high=True)
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        V.vpl_gather_noalloc(ctx.h, sid, gb, vs, view.gather, out)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    after = V.vpl_pool_stats(ctx.h)
+    free1 = torch.cuda.mem_get_info()[0]
+    assert after["high"] == before["used"] == after["used"], (before, after)
+    assert free1 >= free0, (free0, free1)
+    # the same check sees vpl_gather's temporaries
+    V.vpl_pool_stats(ctx.h, reset_high=True)
+    V.vpl_gather(ctx.h, sid, gb, vs, view.gather, out)
+    assert V.vpl_sync(ctx.h, check=False) == 0
+    assert V.vpl_pool_stats(ctx.h)["high"] > after["used"]
