@@ -108,6 +108,8 @@ def lib() -> C.CDLL:
             L.orc_close_order.restype = C.c_int64
             L.orc_ir_path.argtypes = [_P, C.POINTER(_Light), C.POINTER(_Gen), C.c_int64, _D, _D, _I64, _D, _I64]
             L.orc_ir_path.restype = C.c_int64
+            L.orc_flip_ratio.argtypes = [_P, _D, _D, C.c_double, C.c_double, C.c_int32]
+            L.orc_flip_ratio.restype = C.c_double
             L.orc_num_threads.restype = C.c_int32
             L.orc_set_threads.argtypes = [C.c_int32]
             _lib = L
@@ -234,6 +236,17 @@ class OracleScene:
         p = _f64(p, (3,))
         q = _f64(q, (3,))
         return float(lib().orc_segment_margin(self.h, _ptr(p, C.c_double), _ptr(q, C.c_double)))
+
+    def flip_ratio(self, p, q, c: float = 16.0, extra: float = 0.0, ends: int = 3) -> float:
+        """orc_flip_ratio: <= 1 when FP32 rounding (c unit roundoffs of the
+        coordinates, scaled by the incidence and the triangle's shape, plus
+        `extra` of end-point error) can change segment p->q's answer; `ends`
+        selects which end points' distances to a plane count (bit 0 p,
+        bit 1 q)."""
+        p = _f64(p, (3,))
+        q = _f64(q, (3,))
+        return float(lib().orc_flip_ratio(self.h, _ptr(p, C.c_double), _ptr(q, C.c_double), float(c),
+                                          float(extra), int(ends)))
 
     # --- the method --------------------------------------------------------
     def classify(self, cam, d_close, rule: int = 0) -> np.ndarray:

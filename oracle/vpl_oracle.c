@@ -422,6 +422,16 @@ ORC_API void orc_occluded_batch(void *sp, int64_t n, const double *p, const doub
         out[i] = (uint8_t)occluded(s, ld3(p + 3 * i), ld3(q + 3 * i), vis_mode);
 }
 
+/* distance from x to the segment A-B */
+static double seg_dist(d3 x, d3 A, d3 B)
+{
+    d3 ab = sub(B, A);
+    double l2 = dot(ab, ab);
+    double t = l2 > 0.0 ? dot(sub(x, A), ab) / l2 : 0.0;
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    return len(sub(x, add(A, scl(ab, t))));
+}
+
 /* Smallest distance-like margin of segment p->q to flipping its visibility:
  * for every triangle whose plane the segment crosses (or nearly touches), the
  * distance of the crossing point to the triangle's boundary, and the
@@ -448,16 +458,9 @@ ORC_API double orc_segment_margin(void *sp, const double *p3, const double *q3)
         /* distance of x to the triangle's edges (in-plane, signed inside > 0) */
         d3 v0 = s->a[k], v1 = add(v0, s->e1[k]), v2 = add(v0, s->e2[k]);
         d3 vs[3] = {v0, v1, v2};
+        /* distance of x (in the plane) to the triangle's boundary */
         double m_in = INFINITY;
-        for (int e = 0; e < 3; e++) {
-            d3 A = vs[e], B = vs[(e + 1) % 3];
-            d3 ed = sub(B, A);
-            d3 inw = cross(nn, ed);
-            double il = len(inw);
-            if (il == 0.0) continue;
-            double sd = dot(sub(x, A), inw) / il;
-            if (fabs(sd) < m_in) m_in = fabs(sd);
-        }
+        for (int e = 0; e < 3; e++) m_in = dmin(m_in, seg_dist(x, vs[e], vs[(e + 1) % 3]));
         int inside = 1;
         for (int e = 0; e < 3; e++) {
             d3 A = vs[e], B = vs[(e + 1) % 3];
@@ -469,6 +472,69 @@ ORC_API double orc_segment_margin(void *sp, const double *p3, const double *q3)
             if (ep < m) m = ep;
         }
         if (m < best) best = m;
+    }
+    return best;
+}
+
+/* How close segment p->q comes to changing its answer against any triangle,
+ * measured against what FP32 arithmetic can move.  For each triangle whose
+ * plane the segment's line crosses at t in [-1e-3, 1 + 1e-3]:
+ *   - when the segment itself crosses the plane (t in [0, 1]), the in-plane
+ *     distance m_e of the crossing to the triangle's boundary, against
+ *       B_e = (c u (|p|inf + |q|inf + |p - a_k|) + extra) / (cos_k sin_k);
+ *   - when the crossing lies inside the triangle, the distance m_p of an end
+ *     point to its plane (p when ends & 1, q when ends & 2), against
+ *       B_p = (c u (|p|inf + |q|inf + |p - a_k|) + extra) / sin_k.
+ * u = 2^-24 (FP32 unit roundoff); cos_k = |cos| of the angle between the
+ * segment and the triangle's normal; sin_k = the sine of the triangle's
+ * angle at a_k.  Rounding the end points and the products of a
+ * Moller-Trumbore test in FP32 moves its barycentric decisions by a few
+ * u (|p| + |q| + |p - a|) / sin in barycentric length, which the crossing
+ * turns into 1 / cos along the plane, and its segment-parameter decisions
+ * by the same over sin in distance from the plane; `extra` is an absolute
+ * error the end points already carry (e.g. from earlier FP32 bounces).
+ * Returns the smallest ratio m / B: a disagreement between FP32 and FP64 is
+ * explained when it is at most 1. */
+ORC_API double orc_flip_ratio(void *sp, const double *p3, const double *q3, double c, double extra, int32_t ends)
+{
+    const oscene *s = (const oscene *)sp;
+    const double u = 1.0 / 16777216.0;
+    d3 p = ld3(p3), q = ld3(q3), d = sub(q, p);
+    double dl = len(d);
+    double pinf = dmax(fabs(p.x), dmax(fabs(p.y), fabs(p.z)));
+    double qinf = dmax(fabs(q.x), dmax(fabs(q.y), fabs(q.z)));
+    double best = INFINITY;
+    if (dl == 0.0) return best;
+    for (int64_t k = 0; k < s->nt; k++) {
+        double nl = len(s->cr[k]);
+        if (nl == 0.0) continue;
+        d3 nn = scl(s->cr[k], 1.0 / nl);
+        double sp_ = dot(sub(p, s->a[k]), nn), sq_ = dot(sub(q, s->a[k]), nn);
+        double dd = dot(d, nn);
+        if (fabs(dd) == 0.0) continue;
+        double t = -sp_ / dd;
+        if (t < -1e-3 || t > 1.0 + 1e-3) continue;
+        d3 x = add(p, scl(d, t));
+        d3 v0 = s->a[k], v1 = add(v0, s->e1[k]), v2 = add(v0, s->e2[k]);
+        d3 vs[3] = {v0, v1, v2};
+        double me = INFINITY;
+        int inside = 1;
+        for (int e = 0; e < 3; e++) {
+            d3 A = vs[e], B = vs[(e + 1) % 3];
+            me = dmin(me, seg_dist(x, A, B));
+            if (dot(cross(sub(B, A), sub(x, A)), nn) < 0.0) inside = 0;
+        }
+        double cosk = fabs(dd) / dl;
+        double sink = nl / (len(s->e1[k]) * len(s->e2[k]));
+        double base = c * u * (pinf + qinf + len(sub(p, s->a[k]))) + extra;
+        double r = (t >= 0.0 && t <= 1.0) ? me / (base / (cosk * sink)) : INFINITY;
+        if (inside) {
+            double mp = INFINITY;
+            if (ends & 1) mp = dmin(mp, fabs(sp_));
+            if (ends & 2) mp = dmin(mp, fabs(sq_));
+            r = dmin(r, mp / (base / sink));
+        }
+        if (r < best) best = r;
     }
     return best;
 }

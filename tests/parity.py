@@ -1,18 +1,235 @@
 """Helpers shared by the GPU parity tests: tolerances and explanations of
 visibility flips.  Tolerances (per pixel, per component):
     |gpu - ref| <= 1e-4 |ref| + 1e-7 mean(ref)
-VPL positions within 1e-6 of the scene diagonal, fluxes within 1e-6
-relative; a GPU/oracle visibility disagreement counts as a flip when the
-oracle finds the segment within 1e-5 of the scene diagonal of an edge or a
-plane crossing."""
+patch VPL positions within 1e-6 of the scene diagonal, light-path VPL
+positions within a bound derived per VPL from FP32 rounding along its path
+(ir_replay), fluxes within 1e-6 relative.  A GPU/oracle disagreement of a
+segment's answer (a visibility flip, a primary or light-path ray that hits
+another face) is explained when the oracle finds the segment so close to a
+triangle's edge or plane that FP32 rounding can move it across
+(OracleScene.flip_ratio <= 1 with FLIP_C unit roundoffs)."""
+import math
+
 import numpy as np
 
 PIX_RTOL = 1e-4
 PIX_ATOL_FRAC = 1e-7
-POS_TOL = 1e-6     # x scene diagonal
+POS_TOL = 1e-6     # x scene diagonal (patch VPLs, G-buffer points)
 FLUX_RTOL = 1e-6
-FLIP_MARGIN = 1e-5  # x scene diagonal
 FLIP_FRACTION = 1e-5
+U32 = 2.0 ** -24   # FP32 unit roundoff
+# Unit roundoffs (of the coordinates, before the incidence and triangle-shape
+# factors) that FP32 rounding of a segment's end points and of a
+# Moller-Trumbore test can move a decision by: 2 for the end points, 3 each
+# for the cross and dot products of one barycentric coordinate, 2 for the
+# comparison against |det|, with a factor 2 to spare.
+FLIP_C = 16.0
+IR_C = 16.0        # the same count for the t of a light-path hit
+
+
+def flip_explained(osc, p, q, extra: float = 0.0, ends: int = 3) -> bool:
+    """Segment p -> q passes so close to some triangle's edge, or ends so
+    close to a plane (`ends`: bit 0 p, bit 1 q), that FP32 rounding
+    (FLIP_C roundoffs, plus `extra` of end-point error) can change its
+    answer."""
+    return osc.flip_ratio(p, q, FLIP_C, extra, ends) <= 1.0
+
+
+def ir_replay(osc, gen, path: int):
+    """Light path `path` replayed by the oracle, with the bound the GPU's
+    FP32 walk obeys.  Per ray b: E_b bounds |x_gpu - x_oracle| (max norm) of
+    its hit point, by the recurrence
+        E_b = (E_{b-1} + u |o_b| + u t_b |d_b|) / cos_b
+              + IR_C u |o_b - a_k| / (cos_b sin_k) + 2 u |x_b|
+    (u = 2^-24; cos_b the cosine of incidence on the face k hit, sin_k the
+    sine of its angle at vertex a_k): the origin's error and the rounding of
+    the origin and direction move the hit along the plane by 1/cos, the FP32
+    ray parameter t is off by IR_C u |o - a_k| / (cos sin) in length along
+    the ray, and x = o + t d and the next origin round twice.  Returns the
+    replay, the bounds of the front hits and, per ray, the error its origin
+    already carries."""
+    r = osc.ir_path(gen, path)
+    V, T = _verts64(osc), osc.scene.tris
+    E, bounds, carried = 0.0, [], []
+    for b in range(len(r["k"])):
+        carried.append(E)
+        if not r["front"][b]:
+            break
+        k, o, d, t = int(r["k"][b]), r["o"][b], r["d"][b], float(r["t"][b])
+        a, e1, e2 = V[T[k, 0]], V[T[k, 1]] - V[T[k, 0]], V[T[k, 2]] - V[T[k, 0]]
+        cr = np.cross(e1, e2)
+        cos = abs(float(d @ cr)) / (np.linalg.norm(d) * np.linalg.norm(cr))
+        sin = np.linalg.norm(cr) / (np.linalg.norm(e1) * np.linalg.norm(e2))
+        x = o + t * d
+        E = ((E + U32 * np.abs(o).max() + U32 * t * np.linalg.norm(d)) / cos
+             + IR_C * U32 * np.linalg.norm(o - a) / (cos * sin) + 2 * U32 * np.abs(x).max())
+        bounds.append(E)
+    return r, bounds, carried
+
+
+def _verts64(osc):
+    v = getattr(osc, "_verts64", None)
+    if v is None:
+        v = osc._verts64 = osc.scene.verts.astype(np.float64)
+    return v
+
+
+def _ray_end(r, b, reach):
+    """End point of ray b of a replay: twice as far as its hit, or `reach`
+    along it on a miss."""
+    o, d = r["o"][b], r["d"][b]
+    if r["k"][b] >= 0:
+        return o + 2.0 * float(r["t"][b]) * d
+    return o + d * (reach / np.linalg.norm(d))
+
+
+def check_patch_vpls(osc, cam, gen, g, r):
+    """Patch VPLs (Eq. 2, "Realization"): faces and tags bit-exact,
+    positions within POS_TOL of the diagonal, normals to FP32, fluxes within
+    FLUX_RTOL except VPLs whose light sample flips visibility (each
+    explained, at most 1% of them).  Returns the number of flips."""
+    Mc = gen.m_close
+    Ld = osc.scene.diag()
+    assert np.array_equal(g["tri"][:Mc], r["tri"][:Mc])
+    assert np.array_equal(g["tag"][:Mc], r["tag"][:Mc])
+    if Mc == 0:
+        return 0
+    assert np.abs(g["pos"][:Mc] - r["pos"][:Mc]).max() <= POS_TOL * Ld
+    tol_n = 1e-7 if getattr(gen, "patch_rule", 0) == 0 else 1e-6
+    assert np.abs(g["nrm"][:Mc] - r["nrm"][:Mc]).max() <= tol_n
+    gf, rf = g["flux"][:Mc], r["flux"][:Mc]
+    bad = np.nonzero((np.abs(gf - rf) > FLUX_RTOL * np.abs(rf) + 1e-30).any(axis=1))[0]
+    for k in bad:
+        assert _patch_flip_explained(osc, cam, gen, int(k), r), (int(k), gf[k], rf[k])
+    assert len(bad) <= max(1, int(0.01 * Mc)), len(bad)
+    return len(bad)
+
+
+def _light_sample(osc, gen, k, s):
+    import oracle as O
+    L = osc.scene.light
+    w = O.philox4x64_10([k, s, 0, 0], [gen.seed, 2])
+    s1, s2 = (w[0] >> np.uint64(40)) / 16777216.0, (w[1] >> np.uint64(40)) / 16777216.0
+    c = np.array(L.center, np.float32).astype(np.float64)
+    if L.type == 1:
+        return c
+    eu = np.array(L.edge_u, np.float32).astype(np.float64)
+    ev = np.array(L.edge_v, np.float32).astype(np.float64)
+    return c + eu * ((2 * s1 - 1) * 0.5) + ev * ((2 * s2 - 1) * 0.5)
+
+
+def _patch_flip_explained(osc, cam, gen, k, r):
+    """Patch VPL k's flux differs: one of its light segments (from the VPL,
+    or under the set-sum rule from the centroid of a face of its stratum, to
+    one of its light samples) grazes an edge or a plane."""
+    eps = float(np.float32(gen.ray_eps))
+    samples = [_light_sample(osc, gen, k, s) for s in range(max(1, gen.light_samples))]
+    starts = [(r["pos"][k], r["nrm"][k])]
+    if getattr(gen, "patch_rule", 0) == 1:
+        starts += _stratum_faces(osc, cam, gen, k, r)
+    for x, n in starts:
+        for y in samples:
+            if flip_explained(osc, x + n * eps, y):
+                return True
+    return False
+
+
+def _stratum_faces(osc, cam, gen, k, r):
+    """(centroid, normal) of each close face overlapping stratum k of the
+    integer area prefix (the set-sum rule's faces)."""
+    V, T = _verts64(osc), osc.scene.tris
+    close = osc.classify(cam, gen.d_close, getattr(gen, "close_rule", 0))
+    order = osc.close_order(close)
+    a, b, c = V[T[order, 0]], V[T[order, 1]], V[T[order, 2]]
+    cr = np.cross(b - a, c - a)
+    A = 0.5 * np.linalg.norm(cr, axis=1)
+    q = np.array([int(np.rint(math.ldexp(float(x), int(r["shift_s"])))) for x in A], dtype=object)
+    f = np.concatenate([[0], np.cumsum(q)])
+    F, K = int(f[-1]), int(gen.m_close)
+    lo, hi = k * F // K, (k + 1) * F // K
+    out = []
+    for m in range(len(order)):
+        if min(int(f[m + 1]), hi) > max(int(f[m]), lo):
+            g = ((a[m] + b[m]) + c[m]) / 3.0
+            out.append((g, cr[m] / np.linalg.norm(cr[m])))
+    return out
+
+
+def check_far_vpls(osc, gen, g, r, g_paths, r_paths):
+    """Light-path VPLs (Sec. 3 step (3)), matched by their (path, bounce)
+    tag.  A tag on both sides: the same face, the position within the bound
+    ir_replay derives for it, the flux times the path count P within
+    FLUX_RTOL (flux = power x albedos / P on each side).  A path whose
+    tags or faces differ between the sides changed course: the oracle
+    replays it and one of its rays up to the first difference must pass an
+    edge or plane within what FP32 rounding and the error its origin
+    carries can move (flip_explained); its VPLs before the difference are
+    compared as above.  Such paths may be at most max(2, 0.5%) of the
+    paths, and P may differ only through them.  Returns the number of
+    divergent paths."""
+    Mc = gen.m_close
+    gt, rt = [int(t) for t in g["tag"][Mc:]], [int(t) for t in r["tag"][Mc:]]
+    if not gt and not rt:
+        return 0
+    gi = {t: i for i, t in enumerate(gt)}
+    ri = {t: i for i, t in enumerate(rt)}
+    assert len(gi) == len(gt) and len(ri) == len(rt), "tags repeat"
+    tail = min(gt[-1], rt[-1])          # above it, tags differ by truncation at m_far
+    first_diff = {}                     # path -> first bounce that differs
+    for t in set(gi) ^ set(ri):
+        if t <= tail:
+            p, b = divmod(t, 16)
+            first_diff[p] = min(first_diff.get(p, 99), b)
+    for t in set(gi) & set(ri):
+        if g["tri"][Mc + gi[t]] != r["tri"][Mc + ri[t]]:
+            p, b = divmod(t, 16)
+            first_diff[p] = min(first_diff.get(p, 99), b)
+    Ld = osc.scene.diag()
+    reach = 2.0 * Ld
+    replays = {}
+    n_checked = 0
+    for t in sorted(set(gi) & set(ri)):
+        p, b = divmod(t, 16)
+        if p in first_diff and b >= first_diff[p]:
+            continue
+        if p not in replays:
+            replays[p] = ir_replay(osc, gen, p)
+        _, bounds, _ = replays[p]
+        i, j = Mc + gi[t], Mc + ri[t]
+        assert g["tri"][i] == r["tri"][j], t
+        err = np.abs(g["pos"][i] - r["pos"][j]).max()
+        assert err <= bounds[b - 1], (t, err, bounds[b - 1])
+        assert np.allclose(g["flux"][i] * g_paths, r["flux"][j] * r_paths, rtol=FLUX_RTOL, atol=0), t
+        n_checked += 1
+    for p, bd in sorted(first_diff.items()):
+        rp, bounds, carried = ir_replay(osc, gen, p)
+        ok = False
+        for b in range(min(bd, len(rp["k"]))):
+            # a ray: only edges count (its origin sits ray_eps off the
+            # surface it leaves, its far end is not a segment end)
+            if flip_explained(osc, rp["o"][b], _ray_end(rp, b, reach), extra=carried[b], ends=0):
+                ok = True
+                break
+        assert ok, ("light path changed course with no ray near an edge", p, bd)
+    n_paths = max(g_paths, r_paths)
+    assert len(first_diff) <= max(2, 0.005 * n_paths), len(first_diff)
+    if not first_diff:
+        assert g_paths == r_paths
+    else:
+        assert abs(g_paths - r_paths) <= max(2, 0.01 * n_paths)
+    assert n_checked >= 0.9 * min(len(gt), len(rt))
+    return len(first_diff)
+
+
+def check_generation(osc, cam, gen, g, r, g_info):
+    """Both halves of one vpl_generate against orc_generate."""
+    assert g_info["n_close"] == r["n_close"]
+    if gen.m_close:
+        assert g_info["f_total"] == r["f_total"] and g_info["shift_s"] == r["shift_s"]
+    flips = check_patch_vpls(osc, cam, gen, g, r)
+    assert g_info["m_far_kept"] == r["m_far_kept"]
+    div = check_far_vpls(osc, gen, g, r, g_info["paths"], r["paths"])
+    return flips, div
 
 
 def pixel_fail(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
@@ -43,7 +260,8 @@ def explain_pixel(oscene, y, ny, vpl, gpu_vis_row, d2_min, eps, L_diag):
     A flip is a pair that both sides evaluate (non-zero shading term and
     non-zero flux: the GPU skips zero-flux VPLs, which patch VPLs in the
     light's shadow are, and the oracle's term excludes the flux) with
-    different V; each must lie within FLIP_MARGIN of an edge or a plane.  A
+    different V; each must pass an edge or a plane within what FP32
+    rounding can move (flip_explained).  A
     pair that only one side evaluates is a cosine or distance decision at
     its rounding boundary: its term must be negligible (1e-6 of the pixel's
     terms), else the pixel is not explained."""
@@ -59,8 +277,10 @@ def explain_pixel(oscene, y, ny, vpl, gpu_vis_row, d2_min, eps, L_diag):
         ok = bool(np.abs(term[one_sided]).sum() <= 1e-6 * max(float(np.abs(term[traced]).sum()), 1e-300))
     if not flips.any():
         return 0, ok, 0.0
-    _, _, margin = oscene.pairs(y, ny, vpl, d2_min, eps, vis_mode=0, want_margin=flips)
-    ok = ok and bool((margin[flips] <= FLIP_MARGIN * L_diag).all())
+    p = np.asarray(y, np.float64) + np.asarray(ny, np.float64) * eps
+    X, N = np.asarray(vpl["pos"], np.float64), np.asarray(vpl["nrm"], np.float64)
+    for i in np.nonzero(flips)[0]:
+        ok = ok and flip_explained(oscene, p, X[i] + N[i] * eps)
     return int(flips.sum()), ok, float(np.abs(term[flips]).sum())
 
 
@@ -84,7 +304,7 @@ def image_errors(got, ref, keep=None) -> dict:
 def explain_failing_pixels(V, torch, ctx, sid, osc, gbuf, vset, params, g, v, got, ref, L_diag):
     """Pixels outside the pixel tolerance, each explained by visibility flips
     (the GPU's visibility bits of that pixel against the oracle's on the same
-    inputs `g`, `v`, every flip within FLIP_MARGIN of an edge or a plane).
+    inputs `g`, `v`, every flip explained by flip_explained).
     Returns (failing pixel indices, total flips)."""
     bad = np.nonzero(pixel_fail(got, ref))[0]
     if not len(bad):
@@ -185,17 +405,28 @@ def check_precision_report(report: dict) -> None:
             <= report["fp16_plain"]["vs_fp64_fp16_inputs"]["mean_rel"] * 1.25 + 1e-9)
 
 
-def explain_render_pixels(V, torch, ctx, sid, osc, view, img, pix, ref_img, same_tri, L_diag):
+def vpl_rows(vs) -> dict:
+    """A device VPL set (FP32 rows) as FP64 arrays: position, face, normal,
+    tag, flux."""
+    pos, nrm = vs.pos.cpu().numpy(), vs.nrm.cpu().numpy()
+    return dict(pos=pos[:, :3].astype(np.float64), tri=pos[:, 3].copy().view(np.int32).astype(np.int64),
+                nrm=nrm[:, :3].astype(np.float64), tag=nrm[:, 3].copy().view(np.int32).astype(np.int64),
+                flux=vs.flux.cpu().numpy()[:, :3].astype(np.float64))
+
+
+def explain_render_pixels(V, torch, ctx, sid, osc, view, img, pix, ref_img, ref_vpl, same_tri, L_diag):
     """Pixels of a full-size vpl_render (the benchmark's launch) that are
     outside the pixel tolerance against the oracle's whole pipeline, each
     explained.  The render is first checked to equal the G-buffer, the
-    generation and the gather called one by one (bit for bit).  A failing
-    pixel is then recomputed by the oracle's gather from the GPU's own
-    G-buffer row and VPL rows: if it passes, the difference came from the
-    FP32 inputs (bounded by the generation parity tests).  If not, the
-    GPU's visibility bits of that pixel are taken with its whole tile as one
-    packet, exactly as in the render, and the pixel must be explained by
-    flips.  Returns (failing, failing on the GPU's inputs, flips)."""
+    generation and the gather called one by one (bit for bit), and the
+    GPU's VPL rows to equal the oracle's (`ref_vpl`) within the generation
+    tolerances (check_generation).  Only then is a failing pixel recomputed
+    by the oracle's gather from the GPU's own G-buffer row and VPL rows: if
+    it passes, the difference came from the FP32 inputs, which the checks
+    above bound.  If not, the GPU's visibility bits of that pixel are taken
+    with its whole tile as one packet, exactly as in the render, and the
+    pixel must be explained by flips.  Returns (failing, failing on the
+    GPU's inputs, flips)."""
     cam = view.camera
     W_, H_ = cam.width, cam.height
     gb = V.GBuffer.empty(W_, H_)
@@ -206,7 +437,9 @@ def explain_render_pixels(V, torch, ctx, sid, osc, view, img, pix, ref_img, same
     out = torch.zeros((W_ * H_, 4), dtype=torch.float32, device="cuda")
     V.vpl_gather(ctx.h, sid, gb, vs, view.gather, out)
     assert V.vpl_sync(ctx.h, check=False) == 0
+    info = V.vpl_generate_info(ctx.h)
     assert np.array_equal(out.cpu().numpy()[pix], img[pix])
+    check_generation(osc, cam, view.gen, vpl_rows(vs), ref_vpl, info)
     bad = np.asarray(pix)[pixel_fail(img[pix], ref_img) & same_tri]
     if not len(bad):
         return 0, 0, 0

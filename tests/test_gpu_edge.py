@@ -59,10 +59,10 @@ def _parity(orc, osc, view, img, V=None, ctx=None, sid=None, max_bad_frac=0.005)
         if len(img) >= 400:
             assert same.mean() >= 0.95
         # each pixel whose primary ray hits another triangle passes an edge
-        eye, Ld = np.array(cam.eye, np.float64), osc.scene.diag()
+        eye = np.array(cam.eye, np.float32).astype(np.float64)
         for k in np.nonzero(~same)[0]:
             q = r["gbuffer"]["pos"][k] if r["gbuffer"]["tri"][k] >= 0 else gpos[k, :3].astype(np.float64)
-            assert osc.segment_margin(eye, eye + 1.01 * (q - eye)) <= PY.FLIP_MARGIN * Ld * 10, int(k)
+            assert PY.flip_explained(osc, eye, eye + 2.0 * (q - eye)), int(k)
     bad = PY.pixel_fail(img, r["image"]) & same
     assert bad.sum() <= max(1, max_bad_frac * len(img)), int(bad.sum())
     return r

@@ -2,10 +2,12 @@
 same seeded inputs (Jin et al., arXiv 2203.11484, Sec. 3 and Eqs. 1-2).
 
   Philox words, close-range sets, patch triangle assignment, VPL tags: bit-exact
-  VPL positions: within 1e-6 of the scene diagonal; fluxes: 1e-6 relative
+  patch VPL positions: within 1e-6 of the scene diagonal; light-path VPL
+  positions: within the bound derived per VPL from FP32 rounding along its
+  path; fluxes: 1e-6 relative
   pixels: |gpu - ref| <= 1e-4 |ref| + 1e-7 mean(ref), except pixels whose
-  error is explained by visibility flips (<= 1e-5 of the pairs, each within
-  1e-5 of the scene diagonal of an edge or plane)
+  error is explained by visibility flips (<= 1e-5 of the pairs, each passing
+  an edge or plane within what FP32 rounding can move)
 """
 import math
 
@@ -99,30 +101,38 @@ def test_bvh_visibility_and_closest_hit(V, ctx, which, request):
     Ld = sc.diag()
     rng = np.random.default_rng(11)
     lo, hi = sc.verts.min(0), sc.verts.max(0)
-    n = 20000
+    n = 200000
     P = rng.uniform(lo, hi, size=(n, 3)).astype(np.float32)
     Q = rng.uniform(lo, hi, size=(n, 3)).astype(np.float32)
-    # segments occluded test
+    # segments occluded test: at most 1e-5 of the segments differ, each explained
     for brute in ([0, 1] if which == "cornell" else [0]):
         occ, _ = _ray_queries(V, ctx, sid, P, Q, 0, brute)
         ref = osc.occluded(P.astype(np.float64), Q.astype(np.float64), vis_mode=0)
         diff = np.nonzero((occ != 0) != ref)[0]
-        assert len(diff) <= max(2, int(1e-3 * n)), (brute, len(diff))
+        print(which, "brute" if brute else "bvh", "segments differing:", len(diff), "of", n)
+        assert len(diff) <= max(1, int(PY.FLIP_FRACTION * n)), (brute, len(diff))
         for i in diff:
-            assert osc.segment_margin(P[i], Q[i]) <= PY.FLIP_MARGIN * Ld
+            assert PY.flip_explained(osc, P[i], Q[i]), i
     # closest hit along P + t (Q - P)
     D = (Q - P).astype(np.float32)
     tri, t = _ray_queries(V, ctx, sid, P, D, 1, 0)
     rtri, rt = osc.closest(P.astype(np.float64), D.astype(np.float64), 0.0, 0)
     same = tri == rtri
-    assert same.mean() > 0.999
+    # a closest hit is not a pair's visibility: faces that coincide (a box
+    # standing on the floor) or share an edge make equal-t ties common in
+    # these scenes, so the bound is 1e-3 of the rays, each one explained
+    assert (~same).sum() <= max(2, 1e-3 * n)
     hit = same & (tri >= 0)
     assert np.allclose(t[hit], rt[hit], rtol=1e-5, atol=1e-6)
+    n_tie = 0
     for i in np.nonzero(~same)[0]:
-        # different triangle: the ray grazes an edge, or two hits are at equal t
+        # different triangle: two hits at equal t (faces that touch), or the
+        # ray passes an edge within FP32 reach
         near_tie = (tri[i] >= 0 and rtri[i] >= 0 and abs(t[i] - rt[i]) <= 1e-5 * max(1.0, rt[i]))
+        n_tie += near_tie
         q = P[i] + D[i] * (rt[i] if rtri[i] >= 0 else t[i])
-        assert near_tie or osc.segment_margin(P[i], P[i] + 2 * (q - P[i])) <= PY.FLIP_MARGIN * Ld
+        assert near_tie or PY.flip_explained(osc, P[i], P[i] + 2 * (q - P[i]), ends=0), i
+    print(which, "closest hits differing:", int((~same).sum()), "of", n, "equal-t ties", n_tie)
 
 
 # ---------------------------------------------------------------------------
@@ -154,11 +164,11 @@ def test_gbuffer_parity(V, ctx, which, request):
     assert np.abs(g["nrm"][pix][ok] - ref["nrm"][ok]).max() <= 1e-7
     assert np.array_equal(g["rho"][pix][ok], ref["rho"][ok])
     # pixels that hit another triangle: the primary ray passes an edge
-    frame_eye = np.array(cam.eye, np.float64)
+    frame_eye = np.array(cam.eye, np.float32).astype(np.float64)
     for k in np.nonzero(~same)[0]:
         q = ref["pos"][k] if ref["tri"][k] >= 0 else g["pos"][pix[k]]
-        far = frame_eye + 1.01 * (q - frame_eye)
-        assert osc.segment_margin(frame_eye, far) <= PY.FLIP_MARGIN * Ld * 10
+        far = frame_eye + 2.0 * (q - frame_eye)
+        assert PY.flip_explained(osc, frame_eye, far), int(pix[k])
 
 
 # ---------------------------------------------------------------------------
@@ -170,90 +180,50 @@ def _generate(V, ctx, sid, cam, gen):
     V.vpl_generate(ctx.h, sid, cam, gen, vs)
     rc = V.vpl_sync(ctx.h, check=False)
     info = V.vpl_generate_info(ctx.h)
-    pos = vs.pos.cpu().numpy()
-    nrm = vs.nrm.cpu().numpy()
-    return dict(pos=pos[:, :3].astype(np.float64), tri=pos[:, 3].copy().view(np.int32).astype(np.int64),
-                nrm=nrm[:, :3].astype(np.float64), tag=nrm[:, 3].copy().view(np.int32).astype(np.int64),
-                flux=vs.flux.cpu().numpy()[:, :3].astype(np.float64), status=rc, info=info), vs
+    return dict(PY.vpl_rows(vs), status=rc, info=info), vs
 
 
-def _light_flip_ok(osc, wl, gen, k, x, n):
-    """A patch VPL whose single light sample's visibility differs: the shadow
-    segment must graze an edge / plane."""
-    import oracle as O
-    L = wl.scene.light
-    w = O.philox4x64_10([k, 0, 0, 0], [gen.seed, 2])
-    s1, s2 = (w[0] >> np.uint64(40)) / 16777216.0, (w[1] >> np.uint64(40)) / 16777216.0
-    c = np.array(L.center, np.float64)
-    y = c + (2 * s1 - 1) * 0.5 * np.array(L.edge_u) + (2 * s2 - 1) * 0.5 * np.array(L.edge_v)
-    xo = x + n * float(np.float32(gen.ray_eps))
-    return osc.segment_margin(xo, y) <= PY.FLIP_MARGIN * wl.scene.diag()
-
-
-@pytest.mark.parametrize("rule", [0, 1])
+@pytest.mark.parametrize("variant", ["centroid", "any_vertex", "ir_only"])
 @pytest.mark.parametrize("which", ["cornell", "room"])
-def test_generate_parity(V, ctx, which, rule, request):
-    """Both close-range rules (centroid; centroid or any vertex)."""
+def test_generate_parity(V, ctx, which, variant, request):
+    """Both close-range rules (centroid; centroid or any vertex), and plain
+    instant radiosity (no close range, every VPL from light paths: the
+    comparison method of the quality study).  Close set, f(N), strata ->
+    faces and tags bit-exact; patch positions and fluxes as the module
+    states (light-sample flips explained); light-path VPLs matched by tag,
+    each within its derived position bound, any path that changed course
+    explained by a ray near an edge."""
     wl, sid, osc = request.getfixturevalue(which)
     view = wl.views[0]
-    cam, gen = view.camera, dataclasses.replace(view.gen, close_rule=rule)
+    cam, gen = view.camera, view.gen
+    if variant == "any_vertex":
+        gen = dataclasses.replace(gen, close_rule=1)
+    elif variant == "ir_only":
+        gen = dataclasses.replace(gen, m_close=0, m_far=gen.m_close + gen.m_far, d_close=0.0)
     g, _ = _generate(V, ctx, sid, cam, gen)
     r = osc.generate(cam, gen, vis_mode=0)
     assert g["status"] == 0 and r["status"] == 0
-    info = g["info"]
-    # (1) + (2): close set, quantised areas, strata -> triangles: exact
-    assert info["n_close"] == r["n_close"]
-    assert info["f_total"] == r["f_total"] and info["shift_s"] == r["shift_s"]
-    Mc = gen.m_close
-    assert np.array_equal(g["tri"][:Mc], r["tri"][:Mc])
-    assert np.array_equal(g["tag"][:Mc], r["tag"][:Mc])
-    Ld = wl.scene.diag()
-    assert np.abs(g["pos"][:Mc] - r["pos"][:Mc]).max() <= PY.POS_TOL * Ld
-    assert np.abs(g["nrm"][:Mc] - r["nrm"][:Mc]).max() <= 1e-7
-    gf, rf = g["flux"][:Mc], r["flux"][:Mc]
-    bad = np.nonzero((np.abs(gf - rf) > PY.FLUX_RTOL * np.abs(rf) + 1e-30).any(axis=1))[0]
-    for k in bad:   # only light-sample visibility flips may differ
-        assert (gf[k] == 0).all() != (rf[k] == 0).all(), k
-        assert _light_flip_ok(osc, wl, gen, int(k), r["pos"][k], r["nrm"][k]), k
-    assert len(bad) <= max(1, int(0.01 * Mc))
-    # (3): light paths, matched by (path, bounce) tag
-    assert info["m_far_kept"] == r["m_far_kept"] == gen.m_far
-    gt, rt = g["tag"][Mc:], r["tag"][Mc:]
-    if info["paths"] == r["paths"] and np.array_equal(gt, rt):
-        same = g["tri"][Mc:] == r["tri"][Mc:]
-        assert same.all()
-        assert np.abs(g["pos"][Mc:] - r["pos"][Mc:]).max() <= 100 * PY.POS_TOL * Ld
-        assert np.allclose(g["flux"][Mc:], r["flux"][Mc:], rtol=PY.FLUX_RTOL, atol=0)
-    else:
-        # a light path that grazed an edge changed course: everything before
-        # it still matches exactly
-        first = int(np.argmax(gt != rt)) if not np.array_equal(gt, rt) else len(gt)
-        assert first > 0.5 * len(gt), first
-        assert abs(info["paths"] - r["paths"]) <= max(2, 0.01 * r["paths"])
+    assert g["info"]["m_far_kept"] == r["m_far_kept"] == gen.m_far
+    flips, div = PY.check_generation(osc, cam, gen, g, r, g["info"])
+    print(which, variant, "light-sample flips", flips, "divergent light paths", div, "paths", r["paths"])
 
 
 @pytest.mark.parametrize("which", ["cornell", "room"])
 def test_generate_parity_set_sum(V, ctx, which, request):
     """Set-sum rule: the face of every patch VPL (the one giving its stratum
     the most area) is exact, positions (area-weighted centroids) and normals
-    agree to FP32, fluxes to 1e-6 except where a face's light segment flips
-    between the FP32 and FP64 BVHs (at most 1% of the VPLs)."""
+    agree to FP32, fluxes to 1e-6 except where the light segment of a face
+    of the stratum flips between the FP32 and FP64 BVHs (each explained, at
+    most 1% of the VPLs)."""
     wl, sid, osc = request.getfixturevalue(which)
     view = wl.views[0]
     cam, gen = view.camera, dataclasses.replace(view.gen, patch_rule=1)
     g, _ = _generate(V, ctx, sid, cam, gen)
     r = osc.generate(cam, gen, vis_mode=0)
     assert g["status"] == 0 and r["status"] == 0
-    Mc = gen.m_close
-    assert np.array_equal(g["tri"][:Mc], r["tri"][:Mc])
-    assert np.array_equal(g["tag"][:Mc], r["tag"][:Mc])
-    Ld = wl.scene.diag()
-    assert np.abs(g["pos"][:Mc] - r["pos"][:Mc]).max() <= PY.POS_TOL * Ld
-    assert np.abs(g["nrm"][:Mc] - r["nrm"][:Mc]).max() <= 1e-6
-    gf, rf = g["flux"][:Mc], r["flux"][:Mc]
-    bad = (np.abs(gf - rf) > PY.FLUX_RTOL * np.abs(rf) + 1e-30).any(axis=1)
-    assert bad.mean() <= 0.01, bad.sum()
+    PY.check_generation(osc, cam, gen, g, r, g["info"])
     # the rule changed something on this view: some stratum spans several faces
+    Mc = gen.m_close
     p0 = osc.generate(cam, view.gen, vis_mode=0)
     assert not np.array_equal(p0["pos"][:Mc], r["pos"][:Mc])
 
@@ -386,8 +356,8 @@ def test_render_parity_room_full_size(V, ctx, room):
     g, _ = _gbuffer(V, ctx, sid, view.camera)
     same_tri = g["tri"][pix] == r["gbuffer"]["tri"]
     M = view.gen.m_close + view.gen.m_far
-    n_bad, n_still, flips = PY.explain_render_pixels(V, torch, ctx, sid, osc, view, img, pix, r["image"], same_tri,
-                                                     wl.scene.diag())
+    n_bad, n_still, flips = PY.explain_render_pixels(V, torch, ctx, sid, osc, view, img, pix, r["image"], r["vpl"],
+                                                     same_tri, wl.scene.diag())
     assert n_bad == int(bad.sum())
     assert flips <= max(3, PY.FLIP_FRACTION * len(pix) * M), flips
     assert np.isfinite(img).all()

@@ -46,7 +46,13 @@ def test_rs_parity(V, ctx, which, m, pilot, tol, share, request):
     Ld = wl.scene.diag()
     if g["info"]["paths"] == r["paths"] and np.array_equal(g["tag"], r["tag"]):
         assert np.array_equal(g["tri"], r["tri"])
-        assert np.abs(g["pos"] - r["pos"]).max() <= 100 * PY.POS_TOL * Ld
+        # each kept VPL is a light-path hit: within the bound derived along its path
+        bounds = {}
+        for i, t in enumerate(r["tag"]):
+            p, b = divmod(int(t), 16)
+            if p not in bounds:
+                bounds[p] = PY.ir_replay(osc, gen, p)[1]
+            assert np.abs(g["pos"][i] - r["pos"][i]).max() <= bounds[p][b - 1], int(t)
         # kept for sure (p = 1): the same flux to FP32; kept with p < 1: flux
         # ~ 1 / p, and p = c / cbar follows the pilot estimate, where a pilot
         # pixel whose primary ray or segment grazes an edge can differ
