@@ -108,7 +108,8 @@ template <int VIS, int PREC, bool COUNT, bool DEBUG, bool BATCH>
 __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gather_kernel(SceneView s, GatherArgs a, GatherExtra e, int *status)
 {
     __shared__ float4 stage[kGatherWarps][3][32];
-    __shared__ int stack[kGatherWarps][kStackMax]; // per-warp traversal stacks
+    __shared__ int stack[kGatherWarps][kWalkStack]; // per-warp traversal stacks
+    __shared__ __align__(16) float nodebuf[kGatherWarps][kBeamBuf]; // per-warp node rows (beam walk)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gfmt = PREC == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     const float eps = a.ray_eps, d2min = a.d2_min;
@@ -204,7 +205,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                 bool vis = true;
                 if (VIS == VPL_VIS_BVH) {
                     const float3 q = fma3(f3(xn), eps, f3(xp));
-                    vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), occ_cache, occ_cache2, stack[wid], status, wc);
+                    vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), q, occ_cache, occ_cache2, stack[wid],
+                                                nodebuf[wid], status, wc);
                 } else if (VIS == VPL_VIS_BRUTE) {
                     const float3 q = fma3(f3(xn), eps, f3(xp));
                     vis = !warp_occluded_brute<COUNT>(s, want, make_ray(o, q - o), wc);

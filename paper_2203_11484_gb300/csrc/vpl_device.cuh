@@ -16,6 +16,15 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kDepthMax = 96;            // binary hierarchy depth, checked when a scene is built
 constexpr int kStackMax = 160;           // >= 3 x levels of the 4-wide tree (<= 53) + 1
 constexpr int kTraversalLimit = 1 << 16; // node visits per query before giving up
+#ifndef VPL_BEAM
+#define VPL_BEAM 1                       // shadow packets take the beam walk when they can
+#endif
+#ifndef VPL_BEAM_PAD
+#define VPL_BEAM_PAD 3.814697265625e-06f // beam boxes widened by this x (|q| + |E|): 2^-18
+#endif
+#ifndef VPL_BEAM_WIDTH
+#define VPL_BEAM_WIDTH 0.1f              // widest beam (spread of directions / length) walked as one
+#endif
 constexpr float kPi = 3.14159265358979323846f;
 constexpr double kPiD = 3.14159265358979323846;
 
@@ -586,23 +595,201 @@ __device__ __forceinline__ bool packet_walk(const SceneView &s, bool want, const
     return occl;
 }
 
+// --------------------------------------------------------------------------
+// Beam walk for shadow packets whose segments all end at one point.  The 32
+// segments of a packet run from the pixels' points o_l to the same VPL point
+// q, so every point of them is q + s e with s in [0, 1] and e = o_l - q in
+// the box E = [El, Eh] (per axis, over the live lanes).  When no axis of E
+// contains 0, a child box B can meet a segment only if
+//     max(0, max_a min_e s_in_a(e)) <= min(1, min_a max_e s_out_a(e)),
+// and since (P - q_a) / e_a is monotonic in e_a on E_a, each extreme is one
+// of the two products with 1/El_a and 1/Eh_a.  That test is one per child
+// box for the whole packet, not one per lane: each step takes up to
+// kBeamNodes nodes off the stack, four lanes per node, one lane per child.
+// The boxes are widened by delta = 2^-18 (|q| + |E|) in the test, far more
+// than the FP32 rounding of the test and of the per-lane slab tests, so it
+// never drops a box a lane's own segment enters.  Leaf children the beam
+// keeps are tested per lane exactly as in packet_walk (the same slab test on
+// the lane's own segment, then its triangles), and a segment that enters a
+// leaf box enters every ancestor box (the FP32 slab test is monotonic under
+// box inclusion), so each lane tests the same triangles as in packet_walk
+// and the answer is the same bit for bit.  A packet whose E spreads over
+// more than VPL_BEAM_WIDTH of its length (a tile across a depth edge) keeps
+// the per-lane walk: its beam would cover far more of the scene than its
+// segments.
+// --------------------------------------------------------------------------
+constexpr int kBeamNodes = 8;    // nodes tested per step (four lanes each)
+constexpr int kBeamStack = 512;  // per-warp stack entries of the beam walk
+constexpr int kWalkStack = kBeamStack > kStackMax ? kBeamStack : kStackMax;
+// per-warp node buffer of the beam walk: kBeamNodes nodes of 32 floats, each
+// padded to 36 so that the eight nodes' rows fall in different banks
+constexpr int kBeamNodeStride = 36;
+constexpr int kBeamBuf = kBeamNodes * kBeamNodeStride;
+
+// float <-> int with the same order (for warp min / max reductions)
+__device__ __forceinline__ int f2ord(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// (a, a) * (r1, r2) + (c1, c2) -> min and max of the two lanes
+__device__ __forceinline__ void fma_pair(float a, unsigned long long r12, unsigned long long c12, float &lo, float &hi)
+{
+    unsigned long long v;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(v) : "l"(pack2(a, a)), "l"(r12), "l"(c12));
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+    lo = fminf(x, y);
+    hi = fmaxf(x, y);
+}
+
+// ex, ey, ez: the per-lane walk's entry rows (fx, fy, fz of warp_occluded);
+// E lo / hi over live lanes, per axis, with no axis containing 0
+template <bool COUNT>
+__device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const Ray &r, bool occl, int &cache,
+                                       int &cache2, int *stk, float *nbuf, int *status, WarpCounters &wc, float3 q,
+                                       float3 El, float3 Eh, int fx, int fy, int fz)
+{
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, k = lane & 3;
+    // the beam: reciprocals of E's ends, box widening, plane constants
+    const float r1x = __frcp_rn(El.x), r2x = __frcp_rn(Eh.x);
+    const float r1y = __frcp_rn(El.y), r2y = __frcp_rn(Eh.y);
+    const float r1z = __frcp_rn(El.z), r2z = __frcp_rn(Eh.z);
+    const float emax = fmaxf(fmaxf(fmaxf(fabsf(El.x), fabsf(Eh.x)), fmaxf(fabsf(El.y), fabsf(Eh.y))),
+                             fmaxf(fabsf(El.z), fabsf(Eh.z)));
+    const float delta = VPL_BEAM_PAD * (fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fabsf(q.z)) + emax);
+    const float dx = El.x > 0.0f ? delta : -delta, dy = El.y > 0.0f ? delta : -delta,
+                dz = El.z > 0.0f ? delta : -delta;
+    const unsigned long long rx = pack2(r1x, r2x), ry = pack2(r1y, r2y), rz = pack2(r1z, r2z);
+    const unsigned long long nx = pack2(-(q.x + dx) * r1x, -(q.x + dx) * r2x),
+                             xx = pack2(-(q.x - dx) * r1x, -(q.x - dx) * r2x);
+    const unsigned long long ny = pack2(-(q.y + dy) * r1y, -(q.y + dy) * r2y),
+                             xy = pack2(-(q.y - dy) * r1y, -(q.y - dy) * r2y);
+    const unsigned long long nz = pack2(-(q.z + dz) * r1z, -(q.z + dz) * r2z),
+                             xz = pack2(-(q.z - dz) * r1z, -(q.z - dz) * r2z);
+    // per-lane exact slab terms (the same arithmetic as packet_walk<ORIENTED>)
+    const float sx = r.inv.x, sy = r.inv.y, sz = r.inv.z;
+    const float kx = -r.oinv.x, ky = -r.oinv.y, kz = -r.oinv.z;
+    if (lane == 0) stk[0] = 0;
+    __syncwarp();
+    int sp = 1, steps = 0;
+    while (true) {
+        // up to kBeamNodes nodes, while their pushes (<= 4 each) fit the stack
+        const int F = sp + 3 * kBeamNodes <= kBeamStack ? (sp < kBeamNodes ? sp : kBeamNodes) : 1;
+        const bool act = g < F;
+        const int node = act ? stk[sp - 1 - g] : 0;
+        sp -= F;
+        __syncwarp();
+        // the four lanes of a node load its rows k and 4 + k (two full 64-byte
+        // halves of the node per instruction) and transpose them through
+        // shared memory, so that lane k holds child k's planes
+        const float4 *p = s.nodes + 8 * (int64_t)node;
+        const float4 ra = __ldg(p + k), rb = __ldg(p + 4 + k);
+        float *nb = nbuf + g * kBeamNodeStride;
+        reinterpret_cast<float4 *>(nb)[k] = ra;
+        reinterpret_cast<float4 *>(nb)[4 + k] = rb;
+        __syncwarp();
+        const float4 meta = reinterpret_cast<const float4 *>(nb)[6];
+        const unsigned m = __float_as_uint(meta.z);
+        const bool isleaf = (m >> k) & 1u, isint = (m >> (4 + k)) & 1u;
+        // this lane's child: the per-lane walk's entry (en*) and exit (ex*) planes
+        const float enx = nb[4 * fx + k], exx = nb[4 * (fx ^ 1) + k];
+        const float eny = nb[4 * fy + k], exy = nb[4 * (fy ^ 1) + k];
+        const float enz = nb[4 * fz + k], exz = nb[4 * (fz ^ 1) + k];
+        bool hit = false;
+        if (act && (isleaf || isint)) {
+            // seen from q, the segment enters through the per-lane exit plane
+            float a0, a1, b0, b1, c0, c1, t;
+            fma_pair(exx, rx, nx, a0, t);
+            fma_pair(enx, rx, xx, t, a1);
+            fma_pair(exy, ry, ny, b0, t);
+            fma_pair(eny, ry, xy, t, b1);
+            fma_pair(exz, rz, nz, c0, t);
+            fma_pair(enz, rz, xz, t, c1);
+            const float sin_ = fmax3(a0, b0, fmaxf(c0, 0.0f));
+            const float sout = fmin3(a1, b1, fminf(c1, 1.0f));
+            hit = sin_ <= sout;
+        }
+        const unsigned lh = __ballot_sync(kFull, hit && isleaf), ih = __ballot_sync(kFull, hit && isint);
+        if (COUNT) {
+            wc.steps++;
+#if VPL_BEAM_STATS
+            if (lane == 0) { wc.visits += F; wc.tests += __popc(lh); }
+#else
+            if (want && !occl) wc.visits += F;
+#endif
+        }
+        // leaves the beam keeps: each live lane tests its own segment exactly
+        unsigned todo = lh;
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const float ax = __shfl_sync(kFull, enx, j), bx = __shfl_sync(kFull, exx, j);
+            const float ay = __shfl_sync(kFull, eny, j), by = __shfl_sync(kFull, exy, j);
+            const float az = __shfl_sync(kFull, enz, j), bz = __shfl_sync(kFull, exz, j);
+            const int lbase = __shfl_sync(kFull, __float_as_int(meta.y), j);
+            const unsigned run = __shfl_sync(kFull, __float_as_uint(meta.w), j) >> (8 * (j & 3));
+            if (want && !occl) {
+                const float te = fmax3(fmaf(ax, sx, kx), fmaf(ay, sy, ky), fmaxf(fmaf(az, sz, kz), 0.0f));
+                const float tx = fmin3(fmaf(bx, sx, kx), fmaf(by, sy, ky), fminf(fmaf(bz, sz, kz), 1.0f));
+                if (te <= tx) {
+                    const int q0 = lbase + (int)(run & 15u), q1 = q0 + (int)((run >> 4) & 7u);
+                    for (int t = q0; t < q1 && !occl; t++) {
+#if !VPL_BEAM_STATS
+                        if (COUNT) wc.tests++;
+#endif
+                        if (seg_block(r, __ldg(s.tri + 3 * t), __ldg(s.tri + 3 * t + 1), __ldg(s.tri + 3 * t + 2))) {
+                            occl = true;
+                            cache2 = cache;
+                            cache = t;
+                        }
+                    }
+                }
+            }
+        }
+        if (lh && __ballot_sync(kFull, want && !occl) == 0) break;
+        if (ih) {
+            const int n_push = __popc(ih);
+            if (sp + n_push > kBeamStack) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
+            // the first node's first child ends on top
+            if (hit && isint)
+                stk[sp + n_push - 1 - __popc(ih & ((1u << lane) - 1u))] =
+                    __float_as_int(meta.x) + __popc((m >> 4) & ((1u << k) - 1u));
+            sp += n_push;
+        }
+        if (sp == 0) break;
+        __syncwarp();
+        if (++steps > kTraversalLimit) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
+    }
+    __syncwarp();
+    return occl;
+}
+
 // `cache`, `cache2` (per lane) are the triangle slots of the last two
 // triangles that blocked one of this lane's segments (most recent first), or
 // -1.  They are tested before the traversal: neighbouring VPLs are usually
 // hidden by the same triangle.  The answer is the same with or without them
 // (a segment is blocked when any triangle blocks it).
+// q: the end point every lane's segment shares (r.o + r.d up to rounding)
 template <bool COUNT>
-__device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, const Ray &r, int &cache,
-                                              int &cache2, int *stk, int *status, WarpCounters &wc)
+__device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, const Ray &r, float3 q, int &cache,
+                                              int &cache2, int *stk, float *nbuf, int *status, WarpCounters &wc)
 {
     bool occl = false;
     if (want && cache >= 0) {
+#if !VPL_BEAM_STATS
         if (COUNT) wc.tests++;
+#endif
         if (seg_block(r, __ldg(s.tri + 3 * cache), __ldg(s.tri + 3 * cache + 1), __ldg(s.tri + 3 * cache + 2)))
             occl = true;
     }
     if (want && !occl && cache2 >= 0) {
+#if !VPL_BEAM_STATS
         if (COUNT) wc.tests++;
+#endif
         if (seg_block(r, __ldg(s.tri + 3 * cache2), __ldg(s.tri + 3 * cache2 + 1), __ldg(s.tri + 3 * cache2 + 2))) {
             occl = true;
             const int x = cache; cache = cache2; cache2 = x;
@@ -621,6 +808,28 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     const unsigned nz = __ballot_sync(kFull, want && !occl && signbit(r.inv.z));
     const bool oriented = (nx == 0 || nx == alive) && (ny == 0 || ny == alive) && (nz == 0 || nz == alive);
     const int fx = nx ? 1 : 0, fy = ny ? 3 : 2, fz = nz ? 5 : 4; // row of each axis' entry plane
+#if VPL_BEAM
+    if (oriented) {
+        // e = o - q = -d over the live lanes, per axis
+        const bool lv = want && !occl;
+        const float ex = -r.d.x, ey = -r.d.y, ez = -r.d.z;
+        const float3 El = make_float3(ord2f(__reduce_min_sync(kFull, lv ? f2ord(ex) : 0x7fffffff)),
+                                      ord2f(__reduce_min_sync(kFull, lv ? f2ord(ey) : 0x7fffffff)),
+                                      ord2f(__reduce_min_sync(kFull, lv ? f2ord(ez) : 0x7fffffff)));
+        const float3 Eh = make_float3(ord2f(__reduce_max_sync(kFull, lv ? f2ord(ex) : (int)0x80000000)),
+                                      ord2f(__reduce_max_sync(kFull, lv ? f2ord(ey) : (int)0x80000000)),
+                                      ord2f(__reduce_max_sync(kFull, lv ? f2ord(ez) : (int)0x80000000)));
+        // no axis of E may contain 0 (every segment crosses each axis' planes
+        // one way), and the beam must be narrow: the spread of E against its
+        // length, else (a tile across a depth edge) the box of directions
+        // covers far more of the scene than the segments do
+        const float spread = fmaxf(fmaxf(Eh.x - El.x, Eh.y - El.y), Eh.z - El.z);
+        const float reach = fmaxf(fmaxf(fmaxf(fabsf(El.x), fabsf(Eh.x)), fmaxf(fabsf(El.y), fabsf(Eh.y))),
+                                  fmaxf(fabsf(El.z), fabsf(Eh.z)));
+        if (El.x * Eh.x > 0.0f && El.y * Eh.y > 0.0f && El.z * Eh.z > 0.0f && spread <= VPL_BEAM_WIDTH * reach)
+            return beam_walk<COUNT>(s, want, r, occl, cache, cache2, stk, nbuf, status, wc, q, El, Eh, fx, fy, fz);
+    }
+#endif
     return oriented ? packet_walk<COUNT, true>(s, want, r, occl, cache, cache2, stk, status, wc, fx, fy, fz)
                     : packet_walk<COUNT, false>(s, want, r, occl, cache, cache2, stk, status, wc, fx, fy, fz);
 }
