@@ -716,11 +716,7 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
         const unsigned lh = __ballot_sync(kFull, hit && isleaf), ih = __ballot_sync(kFull, hit && isint);
         if (COUNT) {
             wc.steps++;
-#if VPL_BEAM_STATS
-            if (lane == 0) { wc.visits += F; wc.tests += __popc(lh); }
-#else
             if (want && !occl) wc.visits += F;
-#endif
         }
         // leaves the beam keeps: each live lane tests its own segment exactly
         unsigned todo = lh;
@@ -738,9 +734,7 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
                 if (te <= tx) {
                     const int q0 = lbase + (int)(run & 15u), q1 = q0 + (int)((run >> 4) & 7u);
                     for (int t = q0; t < q1 && !occl; t++) {
-#if !VPL_BEAM_STATS
                         if (COUNT) wc.tests++;
-#endif
                         if (seg_block(r, __ldg(s.tri + 3 * t), __ldg(s.tri + 3 * t + 1), __ldg(s.tri + 3 * t + 2))) {
                             occl = true;
                             cache2 = cache;
@@ -780,16 +774,12 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
 {
     bool occl = false;
     if (want && cache >= 0) {
-#if !VPL_BEAM_STATS
         if (COUNT) wc.tests++;
-#endif
         if (seg_block(r, __ldg(s.tri + 3 * cache), __ldg(s.tri + 3 * cache + 1), __ldg(s.tri + 3 * cache + 2)))
             occl = true;
     }
     if (want && !occl && cache2 >= 0) {
-#if !VPL_BEAM_STATS
         if (COUNT) wc.tests++;
-#endif
         if (seg_block(r, __ldg(s.tri + 3 * cache2), __ldg(s.tri + 3 * cache2 + 1), __ldg(s.tri + 3 * cache2 + 2))) {
             occl = true;
             const int x = cache; cache = cache2; cache2 = x;
