@@ -621,10 +621,11 @@ __device__ __forceinline__ bool packet_walk(const SceneView &s, bool want, const
 constexpr int kBeamNodes = 8;    // nodes tested per step (four lanes each)
 constexpr int kBeamStack = 512;  // per-warp stack entries of the beam walk
 constexpr int kWalkStack = kBeamStack > kStackMax ? kBeamStack : kStackMax;
-// per-warp node buffer of the beam walk: kBeamNodes nodes of 32 floats, each
+// per-warp node buffer of the beam walk: eight nodes of 32 floats, each
 // padded to 36 so that the eight nodes' rows fall in different banks
 constexpr int kBeamNodeStride = 36;
-constexpr int kBeamBuf = kBeamNodes * kBeamNodeStride;
+constexpr int kBeamBuf = 8 * kBeamNodeStride; // every group of four lanes writes its slot, active or not
+static_assert(kBeamNodes >= 1 && kBeamNodes <= 8, "a warp holds at most eight groups of four lanes");
 
 // float <-> int with the same order (for warp min / max reductions)
 __device__ __forceinline__ int f2ord(float f)
