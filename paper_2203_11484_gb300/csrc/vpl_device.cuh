@@ -719,20 +719,32 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
             wc.steps++;
             if (want && !occl) wc.visits += F;
         }
-        // leaves the beam keeps: each live lane tests its own segment exactly
-        unsigned todo = lh;
-        while (todo) {
-            const int j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const float ax = __shfl_sync(kFull, enx, j), bx = __shfl_sync(kFull, exx, j);
-            const float ay = __shfl_sync(kFull, eny, j), by = __shfl_sync(kFull, exy, j);
-            const float az = __shfl_sync(kFull, enz, j), bz = __shfl_sync(kFull, exz, j);
-            const int lbase = __shfl_sync(kFull, __float_as_int(meta.y), j);
-            const unsigned run = __shfl_sync(kFull, __float_as_uint(meta.w), j) >> (8 * (j & 3));
-            if (want && !occl) {
+        // leaves the beam keeps: each live lane first finds those its own
+        // segment enters (the exact per-lane slab test), then tests their
+        // triangles one leaf per round, every lane on its own leaf
+        if (lh) {
+            unsigned mine = 0, todo = lh;
+            while (todo) {
+                const int j = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const float ax = __shfl_sync(kFull, enx, j), bx = __shfl_sync(kFull, exx, j);
+                const float ay = __shfl_sync(kFull, eny, j), by = __shfl_sync(kFull, exy, j);
+                const float az = __shfl_sync(kFull, enz, j), bz = __shfl_sync(kFull, exz, j);
                 const float te = fmax3(fmaf(ax, sx, kx), fmaf(ay, sy, ky), fmaxf(fmaf(az, sz, kz), 0.0f));
                 const float tx = fmin3(fmaf(bx, sx, kx), fmaf(by, sy, ky), fminf(fmaf(bz, sz, kz), 1.0f));
-                if (te <= tx) {
+                if (te <= tx) mine |= 1u << j;
+            }
+            if (!(want && !occl)) mine = 0;
+            // this lane's own leaf slot, for the lanes whose candidate it is
+            const int my_lbase = __float_as_int(meta.y);
+            const unsigned my_run = __float_as_uint(meta.w) >> (8 * k);
+            while (__any_sync(kFull, mine != 0)) {
+                const bool has = mine != 0;
+                const int j = has ? __ffs(mine) - 1 : lane;
+                mine &= mine - 1;
+                const int lbase = __shfl_sync(kFull, my_lbase, j);
+                const unsigned run = __shfl_sync(kFull, my_run, j);
+                if (has && !occl) {
                     const int q0 = lbase + (int)(run & 15u), q1 = q0 + (int)((run >> 4) & 7u);
                     for (int t = q0; t < q1 && !occl; t++) {
                         if (COUNT) wc.tests++;
@@ -743,6 +755,7 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
                         }
                     }
                 }
+                if (occl) mine = 0;
             }
         }
         if (lh && __ballot_sync(kFull, want && !occl) == 0) break;
