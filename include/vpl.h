@@ -363,7 +363,11 @@ VPL_API int vpl_pool_stats(vpl_ctx *ctx, int32_t reset_high, uint64_t out[3]);
 /* Work counters of one gather launch (not timed): out[0] pairs with a
  * non-empty receiver, [1] pairs with a non-zero shading term (shadow rays),
  * [2] BVH node visits summed over rays, [3] triangle tests summed over rays,
- * [4] blocked rays, [5] warp-wide packet traversal steps. */
+ * [4] blocked rays, [5] warp-wide packet traversal steps.  The counts are
+ * those of each ray's own traversal (the per-lane packet walk, whose node
+ * visits and triangle tests each ray needs); vpl_gather itself may walk
+ * shadow packets with one conservative test per node for the whole packet,
+ * which gives the same visibility with other step counts. */
 VPL_API int vpl_gather_counters(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf,
                                 const vpl_vpl_set *vpls, const vpl_gather_params *params,
                                 uint64_t out[6], vpl_stream stream);

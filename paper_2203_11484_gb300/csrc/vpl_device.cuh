@@ -813,7 +813,10 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     const bool oriented = (nx == 0 || nx == alive) && (ny == 0 || ny == alive) && (nz == 0 || nz == alive);
     const int fx = nx ? 1 : 0, fy = ny ? 3 : 2, fz = nz ? 5 : 4; // row of each axis' entry plane
 #if VPL_BEAM
-    if (oriented) {
+    // the counting instantiation keeps the per-lane walk: its counters are
+    // the work of each ray's own traversal (the algorithmic work of the
+    // roofline), which the beam walk's conservative test would inflate
+    if (!COUNT && oriented) {
         // e = o - q = -d over the live lanes, per axis
         const bool lv = want && !occl;
         const float ex = -r.d.x, ey = -r.d.y, ez = -r.d.z;
