@@ -310,11 +310,69 @@ def batch_section(ctx, n_views: int, precision: int, reps: int = 2) -> dict:
             "graph": "G-buffers + VPL generation per view + one batched gather, captured once"}
 
 
+def large_section(ctx, peak_tflops: float, reps: int = 2) -> dict:
+    """The large configuration: the ~1M-triangle clutter at 1920 x 1080 with
+    32768 VPLs (26214 patch / 6554 light-path), gathered in FP32, FP16
+    attributes + Kahan sums and FP16 attributes + plain sums.  Per precision:
+    the gather's pairs/s (CUDA events, L2 flushed before each launch), its
+    work counters and the FP32 roofline fraction with the same flop
+    constants as the headline."""
+    import torch
+    from paper_2203_11484_gb300 import vpl as V
+    from paper_2203_11484_gb300 import workloads as W
+    wl = W.room1m_workload()
+    sc = wl.scene
+    sid = V.vpl_scene_upload(ctx.h, torch.as_tensor(sc.verts).cuda(), torch.as_tensor(sc.tris).cuda(),
+                             torch.as_tensor(sc.albedo).cuda(), sc.light)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {"workload": wl.name, "tris": sc.n_tris}
+    for name, prec in (("fp32", W.PREC_FP32), ("fp16_kahan", W.PREC_FP16_KAHAN), ("fp16_plain", W.PREC_FP16_PLAIN)):
+        import dataclasses
+        view = wl.views[0]
+        cam, gen = view.camera, view.gen
+        gat = dataclasses.replace(view.gather, precision=prec)
+        fmt = V.FORMAT_FP32 if prec == W.PREC_FP32 else V.FORMAT_FP16
+        M = gen.m_close + gen.m_far
+        gb = V.GBuffer.empty(cam.width, cam.height, fmt=fmt)
+        vs = V.VplSet.empty(M, fmt=fmt)
+        img = torch.zeros((cam.width * cam.height, 4), dtype=torch.float32, device="cuda")
+        V.vpl_gbuffer_build(ctx.h, sid, cam, gb, stream)
+        V.vpl_generate(ctx.h, sid, cam, gen, vs, stream)
+        V.vpl_gather(ctx.h, sid, gb, vs, gat, img, stream)          # warm-up
+        ms = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            V.vpl_gather(ctx.h, sid, gb, vs, gat, img, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        cnt = V.vpl_gather_counters(ctx.h, sid, gb, vs, gat, stream)
+        status = V.vpl_sync(ctx.h, stream, check=False)
+        t = statistics.mean(ms)
+        pairs = cam.width * cam.height * M
+        flops = (cnt[0] * FLOPS_PER_PAIR + cnt[1] * FLOPS_PER_RAY + cnt[2] * FLOPS_PER_NODE
+                 + cnt[3] * FLOPS_PER_TRI)
+        out[name] = {"gather_ms": t, "pairs_per_s": pairs / (t / 1e3), "width": cam.width, "height": cam.height,
+                     "vpls": M, "achieved_tflops": flops / (t / 1e3) / 1e12,
+                     "frac": flops / (t / 1e3) / 1e12 / peak_tflops,
+                     "counters": {"pairs": cnt[0], "shadow_rays": cnt[1], "node_visits": cnt[2],
+                                  "tri_tests": cnt[3], "blocked": cnt[4]},
+                     "device_status": V.STATUS_NAMES.get(status, status)}
+        del gb, vs, img
+    V.vpl_scene_release(ctx.h, sid)
+    return out
+
+
 def serve_section(ctx, n_requests: int, factors, precision: int) -> dict:
     """Poisson arrivals of render requests over two resident scenes (the 200k
     room and the ~1M-triangle clutter); resolution 256^2 .. 1920x1080, VPL
     budgets log-uniform 1k .. 16k.  The rate is a multiple of the measured
-    one-at-a-time capacity.  Continuous batching (4 lanes, groups of up to 8,
+    one-at-a-time capacity.  Continuous batching (two groups in flight, groups
+    of up to 8, generation on a stream per group overlapping the previous
+    group's gather, gathers in admission order on one high-priority stream,
     one batched gather per group) against a plain FIFO queue (one request per
     launch sequence, one at a time), on the same arrivals."""
     import numpy as np
@@ -344,7 +402,7 @@ def serve_section(ctx, n_requests: int, factors, precision: int) -> dict:
     out = {"capacity_views_per_s": capacity, "requests_per_rate": n_requests, "rates": []}
     for f in factors:
         row = {"rate_factor": f, "rate_per_s": f * capacity}
-        for name, lanes, group in (("plain_fifo", 1, 1), ("continuous_batching", 4, 8)):
+        for name, lanes, group in (("plain_fifo", 1, 1), ("continuous_batching", 2, 8)):
             srv = S.Server(S.GpuBackend(ctx.h, sids, lanes), n_tris, lanes=lanes, max_group=group,
                            reserve_bytes=4 << 30)
             st = srv.run(requests(f * capacity))
@@ -604,9 +662,14 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": hout.numel() * 4,
                "ms_per_step": statistics.mean(e_ms)}
 
-    batch = None
+    batch = batch_fp16 = None
     if args.batch_views > 0 and args.workload == "room200k":
         batch = batch_section(ctx, args.batch_views, prec)
+        if prec == W.PREC_FP32:
+            batch_fp16 = batch_section(ctx, args.batch_views, W.PREC_FP16_KAHAN)
+    large = None
+    if args.large and args.workload == "room200k":
+        large = large_section(ctx, peak_tflops)
     serving = None
     if args.serve_requests > 0 and args.workload == "room200k":
         serving = serve_section(ctx, args.serve_requests, [float(x) for x in args.serve_rates.split(",")], prec)
@@ -634,7 +697,7 @@ def run_ours(args):
                 "gather_ms_per_step": gather_in_step_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "wall_s": wall, "direct_term": direct, "batch": batch,
-                "serving": serving}
+                "batch_fp16_kahan": batch_fp16, "large": large, "serving": serving}
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
@@ -654,10 +717,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-views", type=int, default=64,
                     help="views of the batched comparison (0: skip)")
-    ap.add_argument("--serve-requests", type=int, default=24,
+    ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests per arrival rate in the serving comparison (0: skip)")
-    ap.add_argument("--serve-rates", default="1.0,2.0",
+    ap.add_argument("--serve-rates", default="0.5,1.0,1.5",
                     help="arrival rates as multiples of the one-at-a-time capacity")
+    ap.add_argument("--large", type=int, default=1,
+                    help="1: add the 1M-triangle 1920x1080 x 32768 gather in three precisions (0: skip)")
     ap.add_argument("--workload", default="room200k", choices=["room200k", "clutter1m"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16_kahan", "fp16_plain"])
     ap.add_argument("--width", type=int, default=0, help="0: the workload's size")

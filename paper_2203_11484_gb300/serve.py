@@ -2,14 +2,22 @@
 
 Scenes (and their BVHs) stay on the device.  Requests (a view of one scene:
 camera, resolution, VPL budget) arrive over time and wait in a FIFO queue.
-Whenever one of the `lanes` (a CUDA stream each) is idle, the scheduler
-admits the oldest requests of one scene -- up to `max_group` of them, as long
-as their estimated device memory fits what is free -- and launches them as a
+Whenever one of the `lanes` (groups in flight) is free, the scheduler admits
+the oldest requests of one scene -- up to `max_group` of them, as long as
+their estimated device memory fits the budget -- and launches them as a
 group: per request the G-buffer and VPL generation, then ONE batched gather
 for the whole group (vpl_gather_views).  Requests that arrive while others
-are on the GPU are admitted as soon as a lane and memory free up, and groups
-on different lanes overlap on the device.  Every pixel is summed in VPL order
-by one thread, so a request's image is the same alone and in any mix.
+are on the GPU are admitted as soon as a lane and memory free up.
+
+On the device (GpuBackend) the groups form a two-stage pipeline: each
+group's G-buffers and VPL generations run on a stream of its own, and the
+gathers -- the persistent launches that fill the whole GPU -- run on ONE
+high-priority stream in admission order.  So the oldest request's gather
+never shares the SMs with a newer group's gather, while the next group's
+generation overlaps the running gather; requests that queue up behind a
+running gather are batched into the next group.  Every pixel is summed in
+VPL order by one thread, so a request's image is the same alone and in any
+mix.
 
 The scheduler is independent of the GPU: `Backend` launches groups and
 reports completion; `GpuBackend` does it with libvpl.
@@ -178,7 +186,8 @@ def random_requests(rng, scenes: Dict[str, tuple], n: int, rate: float,
 
 
 class GpuBackend(Backend):
-    """Groups on per-lane CUDA streams through libvpl."""
+    """Groups through libvpl: generation on a low-priority stream per lane,
+    gathers on one high-priority stream in launch order."""
 
     def __init__(self, ctx, scene_ids: Dict[str, int], lanes: int):
         import torch
@@ -187,7 +196,8 @@ class GpuBackend(Backend):
         self.V = V
         self.ctx = ctx
         self.sids = scene_ids
-        self.streams = [torch.cuda.Stream() for _ in range(lanes)]
+        self.streams = [torch.cuda.Stream(priority=0) for _ in range(lanes)]
+        self.gather_stream = torch.cuda.Stream(priority=-1)
 
     def free_bytes(self) -> int:
         t = self.torch
@@ -196,7 +206,7 @@ class GpuBackend(Backend):
 
     def launch(self, group: List[Request], lane: int):
         t, V = self.torch, self.V
-        s = self.streams[lane]
+        s, gs = self.streams[lane], self.gather_stream
         gbufs, vsets, outs = [], [], []
         with t.cuda.stream(s):
             for r in group:
@@ -211,9 +221,22 @@ class GpuBackend(Backend):
                 vsets.append(vs)
                 outs.append(out)
                 r.image = out
-            V.vpl_gather_views(self.ctx, self.sids[group[0].scene], gbufs, vsets, outs, group[0].view.gather, s)
+            prepared = t.cuda.Event()
+            prepared.record(s)
+        # the group's buffers were allocated on stream s and are used on gs
+        for x in gbufs:
+            for a in (x.pos, x.nrm, x.albedo):
+                a.record_stream(gs)
+        for x in vsets:
+            for a in (x.pos, x.nrm, x.flux):
+                a.record_stream(gs)
+        for a in outs:
+            a.record_stream(gs)
+        gs.wait_event(prepared)
+        with t.cuda.stream(gs):
+            V.vpl_gather_views(self.ctx, self.sids[group[0].scene], gbufs, vsets, outs, group[0].view.gather, gs)
             ev = t.cuda.Event()
-            ev.record(s)
+            ev.record(gs)
         return (ev, gbufs, vsets)
 
     def done(self, handle) -> bool:

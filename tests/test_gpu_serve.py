@@ -1,6 +1,8 @@
 """Serving with continuous batching on the GPU: requests over two resident
-scenes, admitted into groups on several streams while others run, give the
-same image as each request rendered alone."""
+scenes, admitted into groups while others run (generation on a stream per
+group, gathers in admission order on one stream), give the same image as
+each request rendered alone; the admission estimate bounds the memory a
+group takes."""
 import numpy as np
 import pytest
 
@@ -91,5 +93,39 @@ def test_generations_on_two_streams_at_once_match_one_at_a_time():
             assert V.vpl_sync(ctx.h, check=False) == 0
             for a, b in zip(one, two):
                 assert torch.equal(a.pos, b.pos) and torch.equal(a.nrm, b.nrm) and torch.equal(a.flux, b.flux)
+    finally:
+        ctx.close()
+
+
+def test_estimate_bytes_bounds_what_a_group_takes():
+    """Admission charges estimate_bytes per request; what a group actually
+    takes -- its tensors (G-buffers, VPL sets, images) plus the most the
+    library's pool holds at once for its generations and batched gather
+    (close-set sort, light-path slots, VPL order) -- must stay within it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11484_gb300 import build, vpl as V
+    build.build_library()
+    ctx = V.Context(0)
+    try:
+        room, lo, hi = W.room200k_scene()
+        sid = ctx.upload(room)
+        scenes = {"room": (room, lo, hi, W.ROOM_D_CLOSE)}
+        rng = np.random.default_rng(31)
+        for res, m_range, n in ((((1920, 1080),), (15000, 16000), 1), (((256, 256), (512, 512)), (1000, 4000), 4)):
+            reqs = S.random_requests(rng, scenes, n, rate=100.0, resolutions=res, m_range=m_range)
+            est = sum(S.estimate_bytes(r.view, room.n_tris) for r in reqs)
+            be = S.GpuBackend(ctx.h, {"room": sid}, lanes=1)
+            torch.cuda.synchronize()
+            base = torch.cuda.memory_allocated()
+            torch.cuda.reset_peak_memory_stats()
+            used0 = V.vpl_pool_stats(ctx.h, reset_high=True)["used"]
+            h = be.launch(reqs, 0)
+            torch.cuda.synchronize()
+            assert V.vpl_sync(ctx.h, check=False) == 0
+            took = (torch.cuda.max_memory_allocated() - base) + (V.vpl_pool_stats(ctx.h)["high"] - used0)
+            print("group of", n, "estimate", est, "took", took)
+            assert 0 < took <= est, (took, est)
+            del h
     finally:
         ctx.close()
