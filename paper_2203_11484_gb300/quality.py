@@ -46,6 +46,30 @@ def _interp_m(ms: Sequence[int], errs: Sequence[float], target: float) -> float:
     return float(ms[0]) if target >= errs[0] else float("inf")
 
 
+def equal_rmse(hyb: List[Dict], ir: List[Dict], seeds: int, n_boot: int = 2000, seed: int = 7) -> List[Dict]:
+    """For each hybrid VPL count, the plain-IR VPL count (and render time)
+    that reaches the hybrid's mean RMSE, by log-log interpolation of IR's
+    mean-RMSE curve, with a 90% bootstrap interval: the seeds of every row
+    are resampled with replacement, both curves' means recomputed and the
+    count found again (5th and 95th percentiles; inf when IR's curve never
+    reaches the hybrid's error within the measured counts)."""
+    ir_m = [r["vpls"] for r in ir]
+    ir_t = [r["ms"] for r in ir]
+    rng = np.random.default_rng(seed)
+    boot_ir = [np.array([np.mean(rng.choice(r["errs"], len(r["errs"]))) for _ in range(n_boot)]) for r in ir]
+    out = []
+    for r in hyb:
+        m_ir = _interp_m(ir_m, [q["rmse"] for q in ir], r["rmse"])
+        t_ir = float("inf") if math.isinf(m_ir) else float(np.interp(math.log(m_ir), np.log(ir_m), ir_t))
+        bh = np.array([np.mean(rng.choice(r["errs"], len(r["errs"]))) for _ in range(n_boot)])
+        ratios = np.array([_interp_m(ir_m, [b[k] for b in boot_ir], bh[k]) / r["vpls"] for k in range(n_boot)])
+        lo, hi = np.percentile(ratios, [5, 95], method="nearest")
+        out.append({"hybrid_vpls": r["vpls"], "rmse": r["rmse"], "ir_vpls_for_equal_rmse": m_ir,
+                    "vpl_ratio": m_ir / r["vpls"], "vpl_ratio_90ci": [float(lo), float(hi)],
+                    "time_ratio": t_ir / r["ms"], "ir_ms": t_ir, "hybrid_ms": r["ms"]})
+    return out
+
+
 def study(view: W.View, scene: W.Scene, ms: Sequence[int] = (1024, 2048, 4096, 8192),
           ir_ms: Sequence[int] = (1024, 2048, 4096, 8192, 16384, 32768), seeds: int = 4,
           m_ref: int = 262144, ref_renders: int = 4, alpha: float = 0.75, bias_m: int = 65536,
@@ -117,23 +141,18 @@ def study(view: W.View, scene: W.Scene, ms: Sequence[int] = (1024, 2048, 4096, 8
                     img, t = render_rs(m, 100 + s) if label == "rejection sampling" else render(mc, mf, 100 + s)
                     errs.append(_rmse(img, ref))
                     times.append(t)
+                sd = statistics.pstdev(errs)
                 rows.append({"method": label, "vpls": m, "m_close": mc, "m_far": mf,
-                             "rmse": statistics.mean(errs), "rmse_sd": statistics.pstdev(errs),
-                             "ms": statistics.mean(times)})
+                             "rmse": statistics.mean(errs), "rmse_sd": sd,
+                             "rmse_se": sd / math.sqrt(max(1, len(errs) - 1)),
+                             "rmse_median": statistics.median(errs), "errs": errs,
+                             "ms": statistics.median(times)})
             return rows
 
         hyb = curve("hybrid", ms, alpha)
         ir = curve("instant radiosity", ir_ms, 0.0)
         rs = curve("rejection sampling", ms, 0.0)
-        ir_m = [r["vpls"] for r in ir]
-        ir_e = [r["rmse"] for r in ir]
-        ir_t = [r["ms"] for r in ir]
-        equal = []
-        for r in hyb:
-            m_ir = _interp_m(ir_m, ir_e, r["rmse"])
-            t_ir = float("inf") if math.isinf(m_ir) else float(np.interp(math.log(m_ir), np.log(ir_m), ir_t))
-            equal.append({"hybrid_vpls": r["vpls"], "rmse": r["rmse"], "ir_vpls_for_equal_rmse": m_ir,
-                          "vpl_ratio": m_ir / r["vpls"], "time_ratio": t_ir / r["ms"]})
+        equal = equal_rmse(hyb, ir, seeds)
         same_m = [{"vpls": r["vpls"], "rmse_hybrid": r["rmse"],
                    "rmse_ir": next(q["rmse"] for q in ir if q["vpls"] == r["vpls"]),
                    "rmse_rs": next(q["rmse"] for q in rs if q["vpls"] == r["vpls"])}
@@ -166,18 +185,27 @@ def point_light_scene(scene: W.Scene) -> W.Scene:
 
 
 def markdown(res: Dict, title: str) -> str:
+    def cell(row):
+        return f"{row['rmse']:.3g} +- {row['rmse_se']:.1g} (med {row['rmse_median']:.3g})"
     lines = [f"{title}: reference = instant radiosity with {res['reference']['vpls']} VPLs, "
-             f"{res['pixels']} pixels, mean of {res['seeds']} seeds", "",
-             "| VPLs | RMSE hybrid | RMSE instant radiosity | RMSE rejection sampling | IR / hybrid |",
-             "|---:|---:|---:|---:|---:|"]
+             f"{res['pixels']} pixels, mean +- standard error over {res['seeds']} seeds (median)", "",
+             "| VPLs | RMSE hybrid | RMSE instant radiosity | RMSE rejection sampling | IR / hybrid | ms hybrid / IR / RS |",
+             "|---:|---:|---:|---:|---:|---:|"]
+    by = {(r["method"], r["vpls"]): r for key in ("hybrid", "instant_radiosity", "rejection_sampling")
+          for r in res[key]}
     for r in res["equal_vpls"]:
-        lines.append(f"| {r['vpls']} | {r['rmse_hybrid']:.3g} | {r['rmse_ir']:.3g} | {r['rmse_rs']:.3g} | "
-                     f"{r['ir_over_hybrid']:.2f} |")
-    lines += ["", "| hybrid VPLs | RMSE | IR VPLs for that RMSE | VPL ratio | time ratio |", "|---:|---:|---:|---:|---:|"]
+        m = r["vpls"]
+        h, i, q = by[("hybrid", m)], by[("instant radiosity", m)], by[("rejection sampling", m)]
+        lines.append(f"| {m} | {cell(h)} | {cell(i)} | {cell(q)} | {r['ir_over_hybrid']:.2f} | "
+                     f"{h['ms']:.1f} / {i['ms']:.1f} / {q['ms']:.1f} |")
+    lines += ["", "| hybrid VPLs | hybrid RMSE | IR VPLs for that RMSE | VPL ratio (90% CI) | time ratio |",
+              "|---:|---:|---:|---:|---:|"]
     for r in res["equal_rmse"]:
         m = r["ir_vpls_for_equal_rmse"]
+        lo, hi = r["vpl_ratio_90ci"]
+        fmt = lambda v: "inf" if math.isinf(v) else f"{v:.2f}"
         lines.append(f"| {r['hybrid_vpls']} | {r['rmse']:.3g} | {'> range' if math.isinf(m) else f'{m:.0f}'} | "
-                     f"{r['vpl_ratio']:.2f} | {r['time_ratio']:.2f} |")
+                     f"{fmt(r['vpl_ratio'])} ({fmt(lo)} - {fmt(hi)}) | {fmt(r['time_ratio'])} |")
     b = res.get("hybrid_large")
     if b:
         lines += ["", f"Hybrid with {b['vpls']} VPLs: RMSE {b['rmse']:.3g}, mean {b['mean_ratio']:.3f} x the "
@@ -193,7 +221,7 @@ def main():
     ap.add_argument("--m-ref", type=int, default=262144)
     ap.add_argument("--ref-renders", type=int, default=4)
     ap.add_argument("--alpha", type=float, default=0.75)
-    ap.add_argument("--seeds", type=int, default=4)
+    ap.add_argument("--seeds", type=int, default=16)
     ap.add_argument("--view-seed", type=int, default=1)
     args = ap.parse_args()
     wl = W.room200k_workload(width=args.width, height=args.height, seed=args.view_seed)
