@@ -153,6 +153,7 @@ def study(view: W.View, scene: W.Scene, ms: Sequence[int] = (1024, 2048, 4096, 8
         ir = curve("instant radiosity", ir_ms, 0.0)
         rs = curve("rejection sampling", ms, 0.0)
         equal = equal_rmse(hyb, ir, seeds)
+        ir_m = [r["vpls"] for r in ir]
         same_m = [{"vpls": r["vpls"], "rmse_hybrid": r["rmse"],
                    "rmse_ir": next(q["rmse"] for q in ir if q["vpls"] == r["vpls"]),
                    "rmse_rs": next(q["rmse"] for q in rs if q["vpls"] == r["vpls"])}
