@@ -290,7 +290,8 @@ def batch_section(ctx, n_views: int, precision: int, reps: int = 2) -> dict:
     ms_single = timed(single)
     # tune on the first 16 views (same distribution), then the whole batch
     tuner = BT.BatchRenderer(ctx.h, sid, wl.views[:16], precision)
-    cfg = tuner.autotune(candidates=[(8, 0), (4, 0), (16, 0), (8, 4)])
+    cfg = tuner.autotune(candidates=BT.CANDIDATES)
+    tune_ms = {f"tile_w={k[0]} blocks_per_sm={k[1]} vpl_tile={k[2]}": v for k, v in tuner.tune_ms.items()}
     tuner.close()
     br = BT.BatchRenderer(ctx.h, sid, wl.views, precision)
     br.config = cfg
@@ -305,7 +306,8 @@ def batch_section(ctx, n_views: int, precision: int, reps: int = 2) -> dict:
             "single_view_ms": ms_single, "batched_graph_ms": ms_batch,
             "views_per_s_single": n_views / (ms_single / 1e3), "views_per_s_batched": n_views / (ms_batch / 1e3),
             "pairs_per_s_batched": pairs / (ms_batch / 1e3), "speedup": ms_single / ms_batch,
-            "tuned": {"tile_w": cfg[0], "blocks_per_sm": cfg[1]}, "images_identical": bool(same),
+            "tuned": {"tile_w": cfg[0], "blocks_per_sm": cfg[1], "vpl_tile": cfg[2]},
+            "tuner_ms_first_16_views": tune_ms, "images_identical": bool(same),
             "device_status": V.STATUS_NAMES.get(status, status),
             "graph": "G-buffers + VPL generation per view + one batched gather, captured once"}
 

@@ -140,12 +140,16 @@ typedef struct {
  *  tile_w     pixel tile of one warp: tile_w x (32 / tile_w), tile_w in
  *             {4, 8, 16, 32}; 0 = 8 (8 x 4)
  *  blocks_per_sm  cap on resident blocks per SM of the persistent grid
- *             (0 = as many as fit).  tile_w and blocks_per_sm change speed
- *             only, never the result. */
+ *             (0 = as many as fit)
+ *  vpl_tile   VPLs a warp stages in shared memory at a time (the VPL side
+ *             of the pixel-tile x VPL-tile blocking): 16, 32 or 64; 0 = 64.
+ *             tile_w, blocks_per_sm and vpl_tile change speed only, never
+ *             the result (every pixel sums its VPLs in the same order). */
 typedef struct {
     float d2_min, ray_eps;
     int32_t precision, visibility;
     int32_t tile_w, blocks_per_sm;
+    int32_t vpl_tile;
 } vpl_gather_params;
 
 /* caller-owned device buffers (see the layouts above) */

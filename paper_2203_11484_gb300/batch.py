@@ -7,9 +7,10 @@ take 32-pixel tiles of all views from one queue, so small views do not leave
 the GPU idle and large ones do not serialise.  The whole sequence can be
 captured once into a CUDA graph and replayed.
 
-The gather's tile shape (tile_w) and resident-block cap (blocks_per_sm) only
-change speed, never the images; `autotune` times the candidates on the batch
-itself and keeps the fastest per batch signature.
+The gather's pixel tile shape (tile_w), VPL tile (vpl_tile: VPLs a warp
+stages in shared memory at a time) and resident-block cap (blocks_per_sm)
+only change speed, never the images; `autotune` times the candidates on the
+batch itself and keeps the fastest per batch signature.
 """
 from __future__ import annotations
 
@@ -20,9 +21,11 @@ import torch
 from . import vpl as V
 from . import workloads as W
 
-Config = Tuple[int, int]  # (tile_w, blocks_per_sm)
+Config = Tuple[int, int, int]  # (tile_w, blocks_per_sm, vpl_tile)
 
-CANDIDATES: List[Config] = [(8, 0), (4, 0), (16, 0), (32, 0), (8, 4), (8, 3)]
+# pixel tile x VPL tile, then resident-block caps at the default tiles
+CANDIDATES: List[Config] = ([(tw, 0, vt) for tw in (8, 4, 16, 32) for vt in (64, 32, 16)]
+                            + [(8, 4, 64), (8, 3, 64)])
 _TUNED: Dict[tuple, Config] = {}
 
 
@@ -44,6 +47,7 @@ class BatchRenderer:
         self.base = W.GatherParams(g0.d2_min, g0.ray_eps, precision, g0.visibility)
         self._batches: Dict[int, int] = {}
         self.config: Optional[Config] = None
+        self.tune_ms: Dict[Config, float] = {}   # every candidate's time in the last autotune
         self.graph: Optional[torch.cuda.CUDAGraph] = None
         self.graph_includes_generation = False
 
@@ -62,7 +66,7 @@ class BatchRenderer:
 
     def _params(self, cfg: Config) -> W.GatherParams:
         return W.GatherParams(self.base.d2_min, self.base.ray_eps, self.base.precision, self.base.visibility,
-                              tile_w=cfg[0], blocks_per_sm=cfg[1])
+                              tile_w=cfg[0], blocks_per_sm=cfg[1], vpl_tile=cfg[2] if len(cfg) > 2 else 0)
 
     # ---- the pipeline -----------------------------------------------------
     def prepare(self, stream=None) -> None:
@@ -89,6 +93,7 @@ class BatchRenderer:
         self.prepare()
         V.vpl_sync(self.ctx)
         best, best_ms = None, float("inf")
+        self.tune_ms = {}
         stream = torch.cuda.current_stream()
         for cfg in candidates:
             self.gather(config=cfg)           # warm-up of this shape
@@ -99,6 +104,7 @@ class BatchRenderer:
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
+            self.tune_ms[tuple(cfg)] = ms
             if ms < best_ms:
                 best, best_ms = cfg, ms
         V.vpl_sync(self.ctx)

@@ -1,10 +1,10 @@
 // Primary-ray G-buffer and the per-pixel indirect gather (Eq. 1 indirect
 // term, Sec. 3 pipeline step (4)), plus the diagnostic kernels.
 //
-// Gather organisation: a warp owns an 8 x 4 pixel tile and walks the whole VPL
-// list in chunks of 32.  Each chunk is read with coalesced float4 loads into
-// a per-warp slice of shared memory and then broadcast VPL by VPL to all 32
-// lanes, so the 32 shadow segments of one step all end at the same VPL and
+// Gather organisation: a warp owns an 8 x 4 pixel tile (tile_w x 32 / tile_w)
+// and walks the whole VPL list in VPL tiles of 16, 32 or 64 (vpl_tile).  Each
+// VPL tile is read with coalesced float4 loads into a per-warp slice of
+// shared memory and then broadcast VPL by VPL to all 32 lanes, so the 32 shadow segments of one step all end at the same VPL and
 // start from neighbouring pixels: the warp traverses the BVH as one packet
 // (warp_occluded).  Tiles are handed out dynamically (an atomic counter) to a
 // grid of resident blocks.  Each pixel sums its VPLs in one thread, in the
@@ -18,7 +18,7 @@
 namespace vpl {
 
 constexpr int kGatherWarps = 4;
-constexpr int kTileW = 8, kTileH = 4;
+constexpr int kMaxVplTile = 64; // the largest VPL tile a warp stages
 // resident blocks per SM the gather is compiled for (register budget
 // 65536 / (128 * blocks)); a build-time tuning knob.  The beam walk's state
 // (its interval constants and a lane's child planes) wants ~96 registers:
@@ -109,12 +109,14 @@ struct GatherExtra {
 template <int VIS, int PREC, bool COUNT, bool DEBUG, bool BATCH>
 __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gather_kernel(SceneView s, GatherArgs a, GatherExtra e, int *status)
 {
-    __shared__ float4 stage[kGatherWarps][3][32];
+    __shared__ float4 stage[kGatherWarps][3][kMaxVplTile];
     __shared__ int stack[kGatherWarps][kWalkStack]; // per-warp traversal stacks
     __shared__ __align__(16) float nodebuf[kGatherWarps][kBeamBuf]; // per-warp node rows (beam walk)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gfmt = PREC == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     const float eps = a.ray_eps, d2min = a.d2_min;
+    // VPLs staged per warp at a time (16, 32 or 64; the ABI checks the value)
+    const int vt = a.vpl_tile >= 1 && a.vpl_tile <= kMaxVplTile ? a.vpl_tile : kMaxVplTile;
     WarpCounters wc = {0u, 0u, 0u};
     unsigned long long n_pairs = 0, n_rays = 0, n_blocked = 0;
     while (true) {
@@ -176,27 +178,29 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
         int occ_cache = -1, occ_cache2 = -1;   // last blocking triangles of this pixel
         float ax = 0.0f, ay = 0.0f, az = 0.0f; // running sums
         float cx = 0.0f, cy_ = 0.0f, cz = 0.0f; // Kahan compensation
-        for (int base = 0; base < M; base += 32) {
+        for (int base = 0; base < M; base += vt) {
             // a BVH walk that hit its limit ends the launch early (the method's
             // own degenerate cases, such as an empty close range, do not)
             int st = lane == 0 ? *(volatile int *)status : 0;
             if (__shfl_sync(kFull, st, 0) == VPL_ERR_TRAVERSAL_LIMIT) break;
-            const int i = base + lane;
-            if (i < M) {
-                const int src = ord ? (int)__ldg(ord + i) : i;
-                const float4 vp = __ldg(v_pos + src);
-                float4 vf = load_attr(v_flux, src, gfmt);
-                if (gfmt == VPL_FORMAT_FP16) { // FP16 colour x FP32 magnitude (pos.w)
-                    vf.x *= vp.w;
-                    vf.y *= vp.w;
-                    vf.z *= vp.w;
+            for (int l = lane; l < vt; l += 32) {
+                const int i = base + l;
+                if (i < M) {
+                    const int src = ord ? (int)__ldg(ord + i) : i;
+                    const float4 vp = __ldg(v_pos + src);
+                    float4 vf = load_attr(v_flux, src, gfmt);
+                    if (gfmt == VPL_FORMAT_FP16) { // FP16 colour x FP32 magnitude (pos.w)
+                        vf.x *= vp.w;
+                        vf.y *= vp.w;
+                        vf.z *= vp.w;
+                    }
+                    stage[wid][0][l] = vp;
+                    stage[wid][1][l] = load_attr(v_nrm, src, gfmt);
+                    stage[wid][2][l] = vf;
                 }
-                stage[wid][0][lane] = vp;
-                stage[wid][1][lane] = load_attr(v_nrm, src, gfmt);
-                stage[wid][2][lane] = vf;
             }
             __syncwarp();
-            const int cnt = min(32, M - base);
+            const int cnt = min(vt, M - base);
             for (int j = 0; j < cnt; j++) {
                 const float4 xp = stage[wid][0][j], xn = stage[wid][1][j], xf = stage[wid][2][j];
                 const float3 d = f3(xp) - y;

@@ -646,6 +646,44 @@ __device__ __forceinline__ void fma_pair(float a, unsigned long long r12, unsign
     hi = fmaxf(x, y);
 }
 
+// plane constants of the beam test: reciprocals of E's ends (r*) and the
+// terms -(q -+ delta) r of the widened entry (n*) and exit (x*) planes
+__device__ __forceinline__ void beam_setup(float3 q, float3 El, float3 Eh, unsigned long long &rx,
+                                           unsigned long long &ry, unsigned long long &rz, unsigned long long &nx,
+                                           unsigned long long &xx, unsigned long long &ny, unsigned long long &xy,
+                                           unsigned long long &nz, unsigned long long &xz)
+{
+    const float r1x = __frcp_rn(El.x), r2x = __frcp_rn(Eh.x);
+    const float r1y = __frcp_rn(El.y), r2y = __frcp_rn(Eh.y);
+    const float r1z = __frcp_rn(El.z), r2z = __frcp_rn(Eh.z);
+    const float emax = fmaxf(fmaxf(fmaxf(fabsf(El.x), fabsf(Eh.x)), fmaxf(fabsf(El.y), fabsf(Eh.y))),
+                             fmaxf(fabsf(El.z), fabsf(Eh.z)));
+    const float delta = VPL_BEAM_PAD * (fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fabsf(q.z)) + emax);
+    const float dx = El.x > 0.0f ? delta : -delta, dy = El.y > 0.0f ? delta : -delta,
+                dz = El.z > 0.0f ? delta : -delta;
+    rx = pack2(r1x, r2x);
+    ry = pack2(r1y, r2y);
+    rz = pack2(r1z, r2z);
+    nx = pack2(-(q.x + dx) * r1x, -(q.x + dx) * r2x);
+    xx = pack2(-(q.x - dx) * r1x, -(q.x - dx) * r2x);
+    ny = pack2(-(q.y + dy) * r1y, -(q.y + dy) * r2y);
+    xy = pack2(-(q.y - dy) * r1y, -(q.y - dy) * r2y);
+    nz = pack2(-(q.z + dz) * r1z, -(q.z + dz) * r2z);
+    xz = pack2(-(q.z - dz) * r1z, -(q.z - dz) * r2z);
+}
+
+// E over the lanes with lv set: min and max of e = -d per axis
+__device__ __forceinline__ void beam_extent(bool lv, const Ray &r, float3 &El, float3 &Eh)
+{
+    const float ex = -r.d.x, ey = -r.d.y, ez = -r.d.z;
+    El = make_float3(ord2f(__reduce_min_sync(kFull, lv ? f2ord(ex) : 0x7fffffff)),
+                     ord2f(__reduce_min_sync(kFull, lv ? f2ord(ey) : 0x7fffffff)),
+                     ord2f(__reduce_min_sync(kFull, lv ? f2ord(ez) : 0x7fffffff)));
+    Eh = make_float3(ord2f(__reduce_max_sync(kFull, lv ? f2ord(ex) : (int)0x80000000)),
+                     ord2f(__reduce_max_sync(kFull, lv ? f2ord(ey) : (int)0x80000000)),
+                     ord2f(__reduce_max_sync(kFull, lv ? f2ord(ez) : (int)0x80000000)));
+}
+
 // ex, ey, ez: the per-lane walk's entry rows (fx, fy, fz of warp_occluded);
 // E lo / hi over live lanes, per axis, with no axis containing 0
 template <bool COUNT>
@@ -656,21 +694,8 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
     const int lane = threadIdx.x & 31;
     const int g = lane >> 2, k = lane & 3;
     // the beam: reciprocals of E's ends, box widening, plane constants
-    const float r1x = __frcp_rn(El.x), r2x = __frcp_rn(Eh.x);
-    const float r1y = __frcp_rn(El.y), r2y = __frcp_rn(Eh.y);
-    const float r1z = __frcp_rn(El.z), r2z = __frcp_rn(Eh.z);
-    const float emax = fmaxf(fmaxf(fmaxf(fabsf(El.x), fabsf(Eh.x)), fmaxf(fabsf(El.y), fabsf(Eh.y))),
-                             fmaxf(fabsf(El.z), fabsf(Eh.z)));
-    const float delta = VPL_BEAM_PAD * (fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fabsf(q.z)) + emax);
-    const float dx = El.x > 0.0f ? delta : -delta, dy = El.y > 0.0f ? delta : -delta,
-                dz = El.z > 0.0f ? delta : -delta;
-    const unsigned long long rx = pack2(r1x, r2x), ry = pack2(r1y, r2y), rz = pack2(r1z, r2z);
-    const unsigned long long nx = pack2(-(q.x + dx) * r1x, -(q.x + dx) * r2x),
-                             xx = pack2(-(q.x - dx) * r1x, -(q.x - dx) * r2x);
-    const unsigned long long ny = pack2(-(q.y + dy) * r1y, -(q.y + dy) * r2y),
-                             xy = pack2(-(q.y - dy) * r1y, -(q.y - dy) * r2y);
-    const unsigned long long nz = pack2(-(q.z + dz) * r1z, -(q.z + dz) * r2z),
-                             xz = pack2(-(q.z - dz) * r1z, -(q.z - dz) * r2z);
+    unsigned long long rx, ry, rz, nx, xx, ny, xy, nz, xz;
+    beam_setup(q, El, Eh, rx, ry, rz, nx, xx, ny, xy, nz, xz);
     // per-lane exact slab terms (the same arithmetic as packet_walk<ORIENTED>)
     const float sx = r.inv.x, sy = r.inv.y, sz = r.inv.z;
     const float kx = -r.oinv.x, ky = -r.oinv.y, kz = -r.oinv.z;
@@ -818,14 +843,8 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     // roofline), which the beam walk's conservative test would inflate
     if (!COUNT && oriented) {
         // e = o - q = -d over the live lanes, per axis
-        const bool lv = want && !occl;
-        const float ex = -r.d.x, ey = -r.d.y, ez = -r.d.z;
-        const float3 El = make_float3(ord2f(__reduce_min_sync(kFull, lv ? f2ord(ex) : 0x7fffffff)),
-                                      ord2f(__reduce_min_sync(kFull, lv ? f2ord(ey) : 0x7fffffff)),
-                                      ord2f(__reduce_min_sync(kFull, lv ? f2ord(ez) : 0x7fffffff)));
-        const float3 Eh = make_float3(ord2f(__reduce_max_sync(kFull, lv ? f2ord(ex) : (int)0x80000000)),
-                                      ord2f(__reduce_max_sync(kFull, lv ? f2ord(ey) : (int)0x80000000)),
-                                      ord2f(__reduce_max_sync(kFull, lv ? f2ord(ez) : (int)0x80000000)));
+        float3 El, Eh;
+        beam_extent(want && !occl, r, El, Eh);
         // no axis of E may contain 0 (every segment crosses each axis' planes
         // one way), and the beam must be narrow: the spread of E against its
         // length, else (a tile across a depth edge) the box of directions

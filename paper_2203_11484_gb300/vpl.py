@@ -50,7 +50,8 @@ class vpl_gen_params(C.Structure):
 
 class vpl_gather_params(C.Structure):
     _fields_ = [("d2_min", C.c_float), ("ray_eps", C.c_float), ("precision", C.c_int32),
-                ("visibility", C.c_int32), ("tile_w", C.c_int32), ("blocks_per_sm", C.c_int32)]
+                ("visibility", C.c_int32), ("tile_w", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("vpl_tile", C.c_int32)]
 
 
 class vpl_vpl_set(C.Structure):
@@ -207,6 +208,7 @@ def make_gather(p: W.GatherParams) -> vpl_gather_params:
     s.d2_min, s.ray_eps = float(p.d2_min), float(p.ray_eps)
     s.precision, s.visibility = int(p.precision), int(p.visibility)
     s.tile_w, s.blocks_per_sm = int(getattr(p, "tile_w", 0)), int(getattr(p, "blocks_per_sm", 0))
+    s.vpl_tile = int(getattr(p, "vpl_tile", 0))
     return s
 
 
