@@ -20,11 +20,11 @@ namespace vpl {
 constexpr int kGatherWarps = 4;
 constexpr int kMaxVplTile = 64; // the largest VPL tile a warp stages
 // resident blocks per SM the gather is compiled for (register budget
-// 65536 / (128 * blocks)); a build-time tuning knob.  The beam walk's state
-// (its interval constants and a lane's child planes) wants ~96 registers:
-// 5 blocks measured 1-2% faster than 7 with spills
+// 65536 / (128 * blocks)); a build-time tuning knob.  With the beam walk's
+// constants in shared memory the kernel fits 80 registers without spills:
+// 6 blocks measured fastest (53.7 ms against 54.4 at 5 and 54.2 at 7)
 #ifndef VPL_GATHER_MIN_BLOCKS
-#define VPL_GATHER_MIN_BLOCKS 5
+#define VPL_GATHER_MIN_BLOCKS 6
 #endif
 
 __device__ __forceinline__ float4 load_attr(const void *base, int64_t i, int fmt)
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
 {
     __shared__ float4 stage[kGatherWarps][3][kMaxVplTile];
     __shared__ int stack[kGatherWarps][kWalkStack]; // per-warp traversal stacks
-    __shared__ __align__(16) float nodebuf[kGatherWarps][kBeamBuf]; // per-warp node rows (beam walk)
+    __shared__ __align__(16) float nodebuf[kGatherWarps][kBeamBuf + kBeamConst]; // per-warp node rows (beam walk)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gfmt = PREC == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     const float eps = a.ray_eps, d2min = a.d2_min;

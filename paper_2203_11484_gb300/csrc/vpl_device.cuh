@@ -625,6 +625,9 @@ constexpr int kWalkStack = kBeamStack > kStackMax ? kBeamStack : kStackMax;
 // padded to 36 so that the eight nodes' rows fall in different banks
 constexpr int kBeamNodeStride = 36;
 constexpr int kBeamBuf = 8 * kBeamNodeStride; // every group of four lanes writes its slot, active or not
+constexpr int kBeamConst = 20;                // 9 float pairs of beam constants (+2 to keep 16-byte rows)
+// each warp's slice starts 16-byte aligned (its rows are stored as float4)
+static_assert((kBeamBuf + kBeamConst) % 4 == 0 && kBeamNodeStride % 4 == 0, "16-byte aligned node rows");
 static_assert(kBeamNodes >= 1 && kBeamNodes <= 8, "a warp holds at most eight groups of four lanes");
 
 // float <-> int with the same order (for warp min / max reductions)
@@ -696,6 +699,13 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
     // the beam: reciprocals of E's ends, box widening, plane constants
     unsigned long long rx, ry, rz, nx, xx, ny, xy, nz, xz;
     beam_setup(q, El, Eh, rx, ry, rz, nx, xx, ny, xy, nz, xz);
+    // the constants are the same in every lane: kept in the warp's shared
+    // slice (read back as broadcasts) instead of 18 registers per lane
+    unsigned long long *bc = reinterpret_cast<unsigned long long *>(nbuf + kBeamBuf);
+    if (lane == 0) {
+        bc[0] = rx; bc[1] = nx; bc[2] = xx; bc[3] = ry; bc[4] = ny; bc[5] = xy; bc[6] = rz; bc[7] = nz; bc[8] = xz;
+    }
+    __syncwarp();
     // per-lane exact slab terms (the same arithmetic as packet_walk<ORIENTED>)
     const float sx = r.inv.x, sy = r.inv.y, sz = r.inv.z;
     const float kx = -r.oinv.x, ky = -r.oinv.y, kz = -r.oinv.z;
@@ -729,12 +739,12 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
         if (act && (isleaf || isint)) {
             // seen from q, the segment enters through the per-lane exit plane
             float a0, a1, b0, b1, c0, c1, t;
-            fma_pair(exx, rx, nx, a0, t);
-            fma_pair(enx, rx, xx, t, a1);
-            fma_pair(exy, ry, ny, b0, t);
-            fma_pair(eny, ry, xy, t, b1);
-            fma_pair(exz, rz, nz, c0, t);
-            fma_pair(enz, rz, xz, t, c1);
+            fma_pair(exx, bc[0], bc[1], a0, t);
+            fma_pair(enx, bc[0], bc[2], t, a1);
+            fma_pair(exy, bc[3], bc[4], b0, t);
+            fma_pair(eny, bc[3], bc[5], t, b1);
+            fma_pair(exz, bc[6], bc[7], c0, t);
+            fma_pair(enz, bc[6], bc[8], t, c1);
             const float sin_ = fmax3(a0, b0, fmaxf(c0, 0.0f));
             const float sout = fmin3(a1, b1, fminf(c1, 1.0f));
             hit = sin_ <= sout;
