@@ -209,13 +209,19 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                 const bool lit = xf.x != 0.0f || xf.y != 0.0f || xf.z != 0.0f;
                 const bool want = valid && lit && cosy > 0.0f && cosi > 0.0f && d2 > 0.0f;
                 bool vis = true;
+                // most VPLs light none of a tile's pixels (a cosine or the
+                // flux is zero): the shadow rays are skipped warp-uniformly
                 if (VIS == VPL_VIS_BVH) {
-                    const float3 q = fma3(f3(xn), eps, f3(xp));
-                    vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), q, occ_cache, occ_cache2, stack[wid],
-                                                nodebuf[wid], status, wc);
+                    if (__any_sync(kFull, want)) {
+                        const float3 q = fma3(f3(xn), eps, f3(xp));
+                        vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), q, occ_cache, occ_cache2,
+                                                    stack[wid], nodebuf[wid], status, wc);
+                    }
                 } else if (VIS == VPL_VIS_BRUTE) {
-                    const float3 q = fma3(f3(xn), eps, f3(xp));
-                    vis = !warp_occluded_brute<COUNT>(s, want, make_ray(o, q - o), wc);
+                    if (__any_sync(kFull, want)) {
+                        const float3 q = fma3(f3(xn), eps, f3(xp));
+                        vis = !warp_occluded_brute<COUNT>(s, want, make_ray(o, q - o), wc);
+                    }
                 }
                 if (COUNT) {
                     n_pairs += valid ? 1 : 0;
