@@ -862,7 +862,13 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
         const float spread = fmaxf(fmaxf(Eh.x - El.x, Eh.y - El.y), Eh.z - El.z);
         const float reach = fmaxf(fmaxf(fmaxf(fabsf(El.x), fabsf(Eh.x)), fmaxf(fabsf(El.y), fabsf(Eh.y))),
                                   fmaxf(fabsf(El.z), fabsf(Eh.z)));
-        if (El.x * Eh.x > 0.0f && El.y * Eh.y > 0.0f && El.z * Eh.z > 0.0f && spread <= VPL_BEAM_WIDTH * reach)
+        // every |e_a| at least 1e-30 (|q| + 1): the plane constants (q -+ delta) / e
+        // of the test stay finite, so no extreme is lost to an overflow
+        const float emin = fminf(fminf(fminf(fabsf(El.x), fabsf(Eh.x)), fminf(fabsf(El.y), fabsf(Eh.y))),
+                                 fminf(fabsf(El.z), fabsf(Eh.z)));
+        const float qmax = fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fabsf(q.z));
+        if (El.x * Eh.x > 0.0f && El.y * Eh.y > 0.0f && El.z * Eh.z > 0.0f && spread <= VPL_BEAM_WIDTH * reach &&
+            emin >= 1e-30f * (qmax + 1.0f))
             return beam_walk<COUNT>(s, want, r, occl, cache, cache2, stk, nbuf, status, wc, q, El, Eh, fx, fy, fz);
     }
 #endif
