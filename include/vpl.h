@@ -143,13 +143,20 @@ typedef struct {
  *             (0 = as many as fit)
  *  vpl_tile   VPLs a warp stages in shared memory at a time (the VPL side
  *             of the pixel-tile x VPL-tile blocking): 16, 32 or 64; 0 = 64.
- *             tile_w, blocks_per_sm and vpl_tile change speed only, never
- *             the result (every pixel sums its VPLs in the same order). */
+ *  walk       shadow-packet traversal of the BVH visibility: 0 = the beam
+ *             walk for packets whose segments form a narrow beam (one
+ *             conservative test per child box for the whole packet, exact
+ *             per-lane tests at the leaves) and the per-lane packet walk for
+ *             the others; 1 = the per-lane packet walk for every packet.
+ *             tile_w, blocks_per_sm, vpl_tile and walk change speed only,
+ *             never the result (every pixel sums its VPLs in the same order
+ *             and every segment gets the same answer from either walk). */
 typedef struct {
     float d2_min, ray_eps;
     int32_t precision, visibility;
     int32_t tile_w, blocks_per_sm;
     int32_t vpl_tile;
+    int32_t walk;
 } vpl_gather_params;
 
 /* caller-owned device buffers (see the layouts above) */

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
     const float eps = a.ray_eps, d2min = a.d2_min;
     // VPLs staged per warp at a time (16, 32 or 64; the ABI checks the value)
     const int vt = a.vpl_tile >= 1 && a.vpl_tile <= kMaxVplTile ? a.vpl_tile : kMaxVplTile;
+    const bool beam = a.walk == 0; // narrow shadow packets take the beam walk
     WarpCounters wc = {0u, 0u, 0u};
     unsigned long long n_pairs = 0, n_rays = 0, n_blocked = 0;
     while (true) {
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                     if (__any_sync(kFull, want)) {
                         const float3 q = fma3(f3(xn), eps, f3(xp));
                         vis = !warp_occluded<COUNT>(s, want, make_ray(o, q - o), q, occ_cache, occ_cache2,
-                                                    stack[wid], nodebuf[wid], status, wc);
+                                                    stack[wid], nodebuf[wid], status, wc, beam);
                     }
                 } else if (VIS == VPL_VIS_BRUTE) {
                     if (__any_sync(kFull, want)) {

@@ -816,10 +816,12 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
 // -1.  They are tested before the traversal: neighbouring VPLs are usually
 // hidden by the same triangle.  The answer is the same with or without them
 // (a segment is blocked when any triangle blocks it).
-// q: the end point every lane's segment shares (r.o + r.d up to rounding)
+// q: the end point every lane's segment shares (r.o + r.d up to rounding);
+// beam: narrow packets may take the beam walk (else the per-lane walk only)
 template <bool COUNT>
 __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, const Ray &r, float3 q, int &cache,
-                                              int &cache2, int *stk, float *nbuf, int *status, WarpCounters &wc)
+                                              int &cache2, int *stk, float *nbuf, int *status, WarpCounters &wc,
+                                              bool beam)
 {
     bool occl = false;
     if (want && cache >= 0) {
@@ -851,7 +853,7 @@ __device__ __forceinline__ bool warp_occluded(const SceneView &s, bool want, con
     // the counting instantiation keeps the per-lane walk: its counters are
     // the work of each ray's own traversal (the algorithmic work of the
     // roofline), which the beam walk's conservative test would inflate
-    if (!COUNT && oriented) {
+    if (!COUNT && beam && oriented) {
         // e = o - q = -d over the live lanes, per axis
         float3 El, Eh;
         beam_extent(want && !occl, r, El, Eh);

@@ -83,6 +83,7 @@ class GatherParams:
     tile_w: int = 0           # warp pixel tile width (0 = 8): speed only
     blocks_per_sm: int = 0    # persistent grid cap (0 = occupancy limit): speed only
     vpl_tile: int = 0         # VPLs staged per warp at a time (0 = 64): speed only
+    walk: int = 0             # 0: beam walk for narrow shadow packets, 1: per-lane walk only: speed only
 
 
 @dataclass

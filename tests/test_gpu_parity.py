@@ -361,3 +361,33 @@ def test_render_parity_room_full_size(V, ctx, room):
     assert n_bad == int(bad.sum())
     assert flips <= max(3, PY.FLIP_FRACTION * len(pix) * M), flips
     assert np.isfinite(img).all()
+
+
+# ---------------------------------------------------------------------------
+# the beam walk against the per-lane packet walk: the same segments, so the
+# same visibility, so the same image bit for bit
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP16_KAHAN])
+def test_beam_walk_equals_per_lane_walk(V, ctx, room, prec):
+    """The full 1024 x 1024 x 4096 room launch with walk = 0 (beam walk for
+    narrow packets) and walk = 1 (per-lane packet walk only): identical
+    images, and identical to the per-lane walk for every pixel tile shape."""
+    wl, sid, osc = room
+    view = wl.views[0]
+    cam = view.camera
+    fmt = V.FORMAT_FP32 if prec == W.PREC_FP32 else V.FORMAT_FP16
+    gb = V.GBuffer.empty(cam.width, cam.height, fmt=fmt)
+    vs = V.VplSet.empty(view.gen.m_close + view.gen.m_far, fmt=fmt)
+    V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
+    V.vpl_generate(ctx.h, sid, cam, view.gen, vs)
+    imgs = {}
+    for walk, tw in ((1, 8), (0, 8), (0, 4), (0, 32)):
+        out = torch.zeros((cam.width * cam.height, 4), dtype=torch.float32, device="cuda")
+        params = dataclasses.replace(view.gather, precision=prec, walk=walk, tile_w=tw)
+        V.vpl_gather(ctx.h, sid, gb, vs, params, out)
+        assert V.vpl_sync(ctx.h, check=False) == 0
+        imgs[(walk, tw)] = out
+    ref = imgs[(1, 8)]
+    assert float(ref.max()) > 0
+    for key, img in imgs.items():
+        assert torch.equal(img, ref), key
