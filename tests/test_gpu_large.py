@@ -98,3 +98,25 @@ def test_large_precision_variants_on_crop(large):
     report = PY.precision_report(V, torch, ctx, sid, osc, wl.views[0], pix, wl.scene.diag())
     print("precision report, 1M clutter crop (1024 receivers x 32768 VPLs):", report)
     PY.check_precision_report(report)
+
+
+def test_large_beam_walk_equals_per_lane_walk(large):
+    """The full 1920 x 1080 x 32768 launch on the 1M-triangle clutter with
+    the beam walk (walk = 0) and with the per-lane packet walk only
+    (walk = 1): identical images."""
+    import dataclasses
+    V, ctx, wl, sid, _ = large
+    view = wl.views[0]
+    cam = view.camera
+    gb = V.GBuffer.empty(cam.width, cam.height)
+    vs = V.VplSet.empty(view.gen.m_close + view.gen.m_far)
+    V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
+    V.vpl_generate(ctx.h, sid, cam, view.gen, vs)
+    imgs = []
+    for walk in (0, 1):
+        out = torch.zeros((cam.width * cam.height, 4), dtype=torch.float32, device="cuda")
+        V.vpl_gather(ctx.h, sid, gb, vs, dataclasses.replace(view.gather, walk=walk), out)
+        assert V.vpl_sync(ctx.h, check=False) == 0
+        imgs.append(out)
+    assert float(imgs[1].max()) > 0
+    assert torch.equal(imgs[0], imgs[1])

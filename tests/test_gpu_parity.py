@@ -367,6 +367,30 @@ def test_render_parity_room_full_size(V, ctx, room):
 # the beam walk against the per-lane packet walk: the same segments, so the
 # same visibility, so the same image bit for bit
 # ---------------------------------------------------------------------------
+def test_beam_walk_equals_per_lane_walk_cornell(V, ctx, cornell):
+    """The 64-triangle room (axis-aligned, coplanar and touching faces, the
+    light just under the ceiling) with BVH visibility: both walks give the
+    same image bit for bit, and it matches the brute-force gather."""
+    wl, sid, osc = cornell
+    view = wl.views[0]
+    cam = view.camera
+    gb = V.GBuffer.empty(cam.width, cam.height)
+    vs = V.VplSet.empty(view.gen.m_close + view.gen.m_far)
+    V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
+    V.vpl_generate(ctx.h, sid, cam, view.gen, vs)
+    imgs = []
+    for walk, vis in ((0, W.VIS_BVH), (1, W.VIS_BVH), (0, W.VIS_BRUTE)):
+        out = torch.zeros((cam.width * cam.height, 4), dtype=torch.float32, device="cuda")
+        V.vpl_gather(ctx.h, sid, gb, vs, dataclasses.replace(view.gather, walk=walk, visibility=vis), out)
+        assert V.vpl_sync(ctx.h, check=False) == 0
+        imgs.append(out)
+    assert float(imgs[0].max()) > 0
+    assert torch.equal(imgs[0], imgs[1])
+    # brute force tests every triangle per segment; the BVH walks may differ
+    # from it only where a segment's FP32 box tests and triangle tests disagree
+    assert (imgs[0] != imgs[2]).any(dim=1).float().mean().item() <= 1e-3
+
+
 @pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP16_KAHAN])
 def test_beam_walk_equals_per_lane_walk(V, ctx, room, prec):
     """The full 1024 x 1024 x 4096 room launch with walk = 0 (beam walk for
