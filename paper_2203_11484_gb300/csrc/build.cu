@@ -781,6 +781,9 @@ static cudaError_t lbvh_build(const Exec &ex, const uint64_t *keys, int n, const
 // the triangles are moved into those slots at the end.  Node indices are
 // handed out in allocation order (root 0, then breadth first); the result
 // does not depend on that order, only on the slot contents and their order.
+// Each node is written in two layouts with the same index: per axis (Node4,
+// for the per-ray and per-lane walks) and per child (two float4 per slot,
+// for the beam walk; see BeamNode).
 // ==========================================================================
 constexpr int kCollapseLevels = (kStackMax - 1) / 3; // each level pushes <= 3 stack entries
 
@@ -833,7 +836,7 @@ __device__ __forceinline__ int small_subtree(const int *child, int c, int *tris)
 template <bool EVEN>
 __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, int *count, int *next,
                                       const int *child, const float *leafbox, const float *nodebox, float4 *nodes,
-                                      int *leaf_src)
+                                      float4 *bnodes, int *leaf_src)
 {
     const int n_in = count[level & 1];
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_in; q += gridDim.x * blockDim.x) {
@@ -898,17 +901,23 @@ __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, in
         float lo[3][4], hi[3][4];
         unsigned leafmask = 0, intmask = 0, runs = 0;
         int ji = 0, jl = 0;
+        int ref[4], cnt[4]; // per slot, for the per-child layout
         for (int k = 0; k < 4; k++) {
             const float *b = nullptr;
+            ref[k] = kEmptyRef;
+            cnt[k] = 0;
             if (k < m && leaf[k]) {
                 b = slot[k] < 0 ? leafbox + 6 * (int64_t)(~slot[k]) : nodebox + 6 * (int64_t)slot[k];
                 const int n = small_subtree(child, slot[k], tris);
                 runs |= (unsigned)(jl | (n << 4)) << (8 * k); // offset in the node's run, count
+                ref[k] = ~(lbase + jl);
+                cnt[k] = n;
                 for (int i = 0; i < n; i++) leaf_src[lbase + jl++] = tris[i];
                 leafmask |= 1u << k;
             } else if (k < m) {
                 b = nodebox + 6 * (int64_t)slot[k];
                 qout[pos + ji] = make_int2(slot[k], ibase + ji);
+                ref[k] = ibase + ji;
                 ji++;
                 intmask |= 1u << k;
             }
@@ -916,6 +925,11 @@ __global__ void collapse_level_kernel(int level, const int2 *qin, int2 *qout, in
                 lo[a][k] = b ? b[a] : (a == 1 ? -3.0e38f : 3.0e38f);
                 hi[a][k] = b ? b[3 + a] : (a == 1 ? -3.0e38f : 3.0e38f);
             }
+        }
+        float4 *bo = bnodes + 8 * (int64_t)w.y;
+        for (int k = 0; k < 4; k++) {
+            bo[2 * k] = make_float4(lo[0][k], lo[1][k], lo[2][k], __int_as_float(ref[k]));
+            bo[2 * k + 1] = make_float4(hi[0][k], hi[1][k], hi[2][k], __int_as_float(cnt[k]));
         }
         float4 *o = nodes + 8 * (int64_t)w.y;
         o[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
@@ -945,7 +959,7 @@ __global__ void place_tris_kernel(int T, const int *leaf_src, const float4 *tri_
 // node is written (at most kCollapseLevels levels when the binary depth is
 // within kDepthMax, which the build checks).
 static cudaError_t collapse4(const Exec &ex, int T, bool even, const int *child, const float *leafbox,
-                             const float *nodebox, float4 *nodes, int *leaf_src, bool *done)
+                             const float *nodebox, float4 *nodes, float4 *bnodes, int *leaf_src, bool *done)
 {
     *done = false;
     Tmp qa, qb, cnt, next;
@@ -962,11 +976,11 @@ static cudaError_t collapse4(const Exec &ex, int T, bool even, const int *child,
         if (even)
             collapse_level_kernel<true><<<grid, 256, 0, ex.stream>>>(l, in.as<int2>(), out.as<int2>(), cnt.as<int>(),
                                                                      next.as<int>(), child, leafbox, nodebox, nodes,
-                                                                     leaf_src);
+                                                                     bnodes, leaf_src);
         else
             collapse_level_kernel<false><<<grid, 256, 0, ex.stream>>>(l, in.as<int2>(), out.as<int2>(),
                                                                       cnt.as<int>(), next.as<int>(), child, leafbox,
-                                                                      nodebox, nodes, leaf_src);
+                                                                      nodebox, nodes, bnodes, leaf_src);
         VPL_LAUNCHED(ex);
         const bool last = !even && l + 1 == kCollapseLevels;
         if (last || (l + 1) % 16 == 0) {
@@ -985,7 +999,7 @@ static cudaError_t collapse4(const Exec &ex, int T, bool even, const int *child,
 }
 
 // one triangle: a root with the leaf (slot 0) in slot 0 and three empty slots
-__global__ void single_root_kernel(const float *leafbox, float4 *nodes)
+__global__ void single_root_kernel(const float *leafbox, float4 *nodes, float4 *bnodes)
 {
     const float *a = leafbox;
     const float f = 3.0e38f;
@@ -997,6 +1011,12 @@ __global__ void single_root_kernel(const float *leafbox, float4 *nodes)
     nodes[5] = make_float4(a[5], f, f, f);
     nodes[6] = make_float4(__int_as_float(0), __int_as_float(0), __uint_as_float(1u), __uint_as_float(1u << 4));
     nodes[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    bnodes[0] = make_float4(a[0], a[1], a[2], __int_as_float(~0));
+    bnodes[1] = make_float4(a[3], a[4], a[5], __int_as_float(1));
+    for (int k = 1; k < 4; k++) {
+        bnodes[2 * k] = make_float4(f, -f, f, __int_as_float(kEmptyRef));
+        bnodes[2 * k + 1] = make_float4(f, -f, f, __int_as_float(0));
+    }
 }
 
 __global__ void depth_kernel(int n, const int *parent_int, const int *parent_leaf, int *depth, int *status)
@@ -1029,6 +1049,7 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
     VPL_TRY(dalloc((void **)&sb->idx, sizeof(int32_t) * 3 * T));
     VPL_TRY(dalloc((void **)&sb->tri, sizeof(float4) * 3 * T));
     VPL_TRY(dalloc((void **)&sb->nodes, sizeof(float4) * 8 * (T > 1 ? T - 1 : 1)));
+    VPL_TRY(dalloc((void **)&sb->bnodes, sizeof(float4) * 8 * (T > 1 ? T - 1 : 1)));
     VPL_TRY(dalloc((void **)&sb->nrm, sizeof(float4) * T));
     VPL_TRY(dalloc((void **)&sb->rho, sizeof(float4) * T));
     VPL_TRY(dalloc((void **)&sb->gbox, sizeof(double) * 6));
@@ -1069,7 +1090,7 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
     VPL_TRY(pleaf.alloc(ex, sizeof(int) * T));
     VPL_TRY(pint.alloc(ex, sizeof(int) * (T > 1 ? T - 1 : 1)));
     if (T == 1) {
-        single_root_kernel<<<1, 1, 0, ex.stream>>>(leafbox.as<float>(), sb->nodes);
+        single_root_kernel<<<1, 1, 0, ex.stream>>>(leafbox.as<float>(), sb->nodes, sb->bnodes);
         VPL_LAUNCHED(ex);
         VPL_TRY(cudaMemcpyAsync(sb->tri, trim.p, sizeof(float4) * 3, cudaMemcpyDeviceToDevice, ex.stream));
     } else {
@@ -1088,11 +1109,11 @@ cudaError_t build_scene(const Exec &ex, const float *verts, int64_t n_verts, con
         bool packed = false;
 #if !VPL_BVH_EVEN_COLLAPSE
         VPL_TRY(collapse4(ex, n, false, child.as<int>(), leafbox.as<float>(), nodebox.as<float>(), sb->nodes,
-                          leaf_src.as<int>(), &packed));
+                          sb->bnodes, leaf_src.as<int>(), &packed));
 #endif
         if (!packed)
             VPL_TRY(collapse4(ex, n, true, child.as<int>(), leafbox.as<float>(), nodebox.as<float>(), sb->nodes,
-                              leaf_src.as<int>(), &packed));
+                              sb->bnodes, leaf_src.as<int>(), &packed));
         place_tris_kernel<<<grid_for(T, B), B, 0, ex.stream>>>(n, leaf_src.as<int>(), trim.as<float4>(), sb->tri);
         VPL_LAUNCHED(ex);
     }

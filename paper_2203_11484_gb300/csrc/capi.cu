@@ -23,7 +23,7 @@ struct SceneRec {
 
 void free_scene(SceneBuffers &b)
 {
-    void *ps[] = {b.tri, b.nodes, b.nrm, b.rho, b.verts, b.idx, b.gbox, b.vbox, b.depth};
+    void *ps[] = {b.tri, b.nodes, b.bnodes, b.nrm, b.rho, b.verts, b.idx, b.gbox, b.vbox, b.depth};
     for (void *p : ps)
         if (p) cudaFree(p);
     b = SceneBuffers();
@@ -178,6 +178,7 @@ SceneView view_of(const SceneRec *s)
     v.n_nodes = (int32_t)(s->b.n_tris > 1 ? s->b.n_tris - 1 : 1);
     v.tri = s->b.tri;
     v.nodes = s->b.nodes;
+    v.bnodes = s->b.bnodes;
     v.nrm = s->b.nrm;
     v.rho = s->b.rho;
     v.verts = s->b.verts;

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
 {
     __shared__ float4 stage[kGatherWarps][3][kMaxVplTile];
     __shared__ int stack[kGatherWarps][kWalkStack]; // per-warp traversal stacks
-    __shared__ __align__(16) float nodebuf[kGatherWarps][kBeamBuf + kBeamConst]; // per-warp node rows (beam walk)
+    __shared__ __align__(16) float nodebuf[kGatherWarps][kBeamConst]; // per-warp beam constants
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gfmt = PREC == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     const float eps = a.ray_eps, d2min = a.d2_min;

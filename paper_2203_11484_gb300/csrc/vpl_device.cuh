@@ -36,6 +36,7 @@ struct SceneView {
     int32_t n_nodes;
     const float4 *tri;     // 3 per triangle, BVH leaf order: v0 (w = original id bits), e1, e2
     const float4 *nodes;   // 8 per 4-wide node (see Node4)
+    const float4 *bnodes;  // the same nodes per child, 8 per node (beam walk)
     const float4 *nrm;     // per original triangle: unit normal (FP32 from FP64)
     const float4 *rho;     // per original triangle: albedo
     const float *verts;    // original FP32 vertices
@@ -250,6 +251,11 @@ __device__ __forceinline__ bool seg_block(const Ray &r, float4 v0, float4 e1v, f
 // no segment reaches.
 // --------------------------------------------------------------------------
 constexpr int kEmptyRef = (int)0x80000000;
+// The same node per child (bnodes, same index, 8 float4 = 128 B): slot k in
+// rows 2k = (lo.x, lo.y, lo.z, ref) and 2k + 1 = (hi.x, hi.y, hi.z, cnt),
+// ref >= 0 an internal node, ~triangle slot for a leaf of cnt triangles,
+// kEmptyRef none.  A lane reads its own child's box and reference with two
+// 16-byte loads, the four lanes of a node one 128-byte line.
 
 struct Node4 {
     float4 lx, hx, ly, hy, lz, hz;
@@ -605,7 +611,8 @@ __device__ __forceinline__ bool packet_walk(const SceneView &s, bool want, const
 // and since (P - q_a) / e_a is monotonic in e_a on E_a, each extreme is one
 // of the two products with 1/El_a and 1/Eh_a.  That test is one per child
 // box for the whole packet, not one per lane: each step takes up to
-// kBeamNodes nodes off the stack, four lanes per node, one lane per child.
+// kBeamNodes nodes off the stack, four lanes per node, one lane per child
+// (its box and reference read from the per-child layout, bnodes).
 // The boxes are widened by delta = 2^-18 (|q| + |E|) in the test, far more
 // than the FP32 rounding of the test and of the per-lane slab tests, so it
 // never drops a box a lane's own segment enters.  Leaf children the beam
@@ -621,13 +628,10 @@ __device__ __forceinline__ bool packet_walk(const SceneView &s, bool want, const
 constexpr int kBeamNodes = 8;    // nodes tested per step (four lanes each)
 constexpr int kBeamStack = 512;  // per-warp stack entries of the beam walk
 constexpr int kWalkStack = kBeamStack > kStackMax ? kBeamStack : kStackMax;
-// per-warp node buffer of the beam walk: eight nodes of 32 floats, each
-// padded to 36 so that the eight nodes' rows fall in different banks
-constexpr int kBeamNodeStride = 36;
-constexpr int kBeamBuf = 8 * kBeamNodeStride; // every group of four lanes writes its slot, active or not
-constexpr int kBeamConst = 20;                // 9 float pairs of beam constants (+2 to keep 16-byte rows)
-// each warp's slice starts 16-byte aligned (its rows are stored as float4)
-static_assert((kBeamBuf + kBeamConst) % 4 == 0 && kBeamNodeStride % 4 == 0, "16-byte aligned node rows");
+// per-warp shared slice of the beam walk: 9 float pairs of constants
+// (+2 floats so that each warp's slice stays 16-byte aligned)
+constexpr int kBeamConst = 20;
+static_assert(kBeamConst % 4 == 0, "16-byte aligned per-warp slices");
 static_assert(kBeamNodes >= 1 && kBeamNodes <= 8, "a warp holds at most eight groups of four lanes");
 
 // float <-> int with the same order (for warp min / max reductions)
@@ -687,8 +691,9 @@ __device__ __forceinline__ void beam_extent(bool lv, const Ray &r, float3 &El, f
                      ord2f(__reduce_max_sync(kFull, lv ? f2ord(ez) : (int)0x80000000)));
 }
 
-// ex, ey, ez: the per-lane walk's entry rows (fx, fy, fz of warp_occluded);
-// E lo / hi over live lanes, per axis, with no axis containing 0
+// fx, fy, fz: the per-lane walk's entry rows (odd: the hi plane, the
+// segments run towards -axis); E lo / hi over live lanes, per axis, with no
+// axis containing 0; nbuf: the warp's kBeamConst floats of shared memory
 template <bool COUNT>
 __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const Ray &r, bool occl, int &cache,
                                        int &cache2, int *stk, float *nbuf, int *status, WarpCounters &wc, float3 q,
@@ -696,12 +701,13 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
 {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 2, k = lane & 3;
+    const bool hx = fx & 1, hy = fy & 1, hz = fz & 1; // entry plane is the hi plane
     // the beam: reciprocals of E's ends, box widening, plane constants
     unsigned long long rx, ry, rz, nx, xx, ny, xy, nz, xz;
     beam_setup(q, El, Eh, rx, ry, rz, nx, xx, ny, xy, nz, xz);
     // the constants are the same in every lane: kept in the warp's shared
     // slice (read back as broadcasts) instead of 18 registers per lane
-    unsigned long long *bc = reinterpret_cast<unsigned long long *>(nbuf + kBeamBuf);
+    unsigned long long *bc = reinterpret_cast<unsigned long long *>(nbuf);
     if (lane == 0) {
         bc[0] = rx; bc[1] = nx; bc[2] = xx; bc[3] = ry; bc[4] = ny; bc[5] = xy; bc[6] = rz; bc[7] = nz; bc[8] = xz;
     }
@@ -719,22 +725,16 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
         const int node = act ? stk[sp - 1 - g] : 0;
         sp -= F;
         __syncwarp();
-        // the four lanes of a node load its rows k and 4 + k (two full 64-byte
-        // halves of the node per instruction) and transpose them through
-        // shared memory, so that lane k holds child k's planes
-        const float4 *p = s.nodes + 8 * (int64_t)node;
-        const float4 ra = __ldg(p + k), rb = __ldg(p + 4 + k);
-        float *nb = nbuf + g * kBeamNodeStride;
-        reinterpret_cast<float4 *>(nb)[k] = ra;
-        reinterpret_cast<float4 *>(nb)[4 + k] = rb;
-        __syncwarp();
-        const float4 meta = reinterpret_cast<const float4 *>(nb)[6];
-        const unsigned m = __float_as_uint(meta.z);
-        const bool isleaf = (m >> k) & 1u, isint = (m >> (4 + k)) & 1u;
+        // lane k of a node's four reads child k (its box and reference) from
+        // the per-child layout: the four lanes read the node's 128-byte line
+        const float4 *p = s.bnodes + 8 * (int64_t)node + 2 * k;
+        const float4 blo = __ldg(p), bhi = __ldg(p + 1);
+        const int ref = __float_as_int(blo.w), tcnt = __float_as_int(bhi.w);
+        const bool isint = ref >= 0, isleaf = ref < 0 && ref != kEmptyRef;
         // this lane's child: the per-lane walk's entry (en*) and exit (ex*) planes
-        const float enx = nb[4 * fx + k], exx = nb[4 * (fx ^ 1) + k];
-        const float eny = nb[4 * fy + k], exy = nb[4 * (fy ^ 1) + k];
-        const float enz = nb[4 * fz + k], exz = nb[4 * (fz ^ 1) + k];
+        const float enx = hx ? bhi.x : blo.x, exx = hx ? blo.x : bhi.x;
+        const float eny = hy ? bhi.y : blo.y, exy = hy ? blo.y : bhi.y;
+        const float enz = hz ? bhi.z : blo.z, exz = hz ? blo.z : bhi.z;
         bool hit = false;
         if (act && (isleaf || isint)) {
             // seen from q, the segment enters through the per-lane exit plane
@@ -770,17 +770,14 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
                 if (te <= tx) mine |= 1u << j;
             }
             if (!(want && !occl)) mine = 0;
-            // this lane's own leaf slot, for the lanes whose candidate it is
-            const int my_lbase = __float_as_int(meta.y);
-            const unsigned my_run = __float_as_uint(meta.w) >> (8 * k);
             while (__any_sync(kFull, mine != 0)) {
                 const bool has = mine != 0;
                 const int j = has ? __ffs(mine) - 1 : lane;
                 mine &= mine - 1;
-                const int lbase = __shfl_sync(kFull, my_lbase, j);
-                const unsigned run = __shfl_sync(kFull, my_run, j);
+                const int lref = __shfl_sync(kFull, ref, j);
+                const int lcnt = __shfl_sync(kFull, tcnt, j);
                 if (has && !occl) {
-                    const int q0 = lbase + (int)(run & 15u), q1 = q0 + (int)((run >> 4) & 7u);
+                    const int q0 = ~lref, q1 = q0 + lcnt;
                     for (int t = q0; t < q1 && !occl; t++) {
                         if (COUNT) wc.tests++;
                         if (seg_block(r, __ldg(s.tri + 3 * t), __ldg(s.tri + 3 * t + 1), __ldg(s.tri + 3 * t + 2))) {
@@ -798,9 +795,7 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
             const int n_push = __popc(ih);
             if (sp + n_push > kBeamStack) { latch(status, VPL_ERR_TRAVERSAL_LIMIT); break; }
             // the first node's first child ends on top
-            if (hit && isint)
-                stk[sp + n_push - 1 - __popc(ih & ((1u << lane) - 1u))] =
-                    __float_as_int(meta.x) + __popc((m >> 4) & ((1u << k) - 1u));
+            if (hit && isint) stk[sp + n_push - 1 - __popc(ih & ((1u << lane) - 1u))] = ref;
             sp += n_push;
         }
         if (sp == 0) break;

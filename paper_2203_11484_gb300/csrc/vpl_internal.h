@@ -65,7 +65,7 @@ cudaError_t radix_sort_pairs(const Exec &ex, uint64_t *keys, uint32_t *vals, con
 
 struct SceneBuffers {
     int64_t n_tris = 0, n_verts = 0;
-    float4 *tri = nullptr, *nodes = nullptr, *nrm = nullptr, *rho = nullptr;
+    float4 *tri = nullptr, *nodes = nullptr, *bnodes = nullptr, *nrm = nullptr, *rho = nullptr;
     float *verts = nullptr;
     int32_t *idx = nullptr;
     double *gbox = nullptr; // [6]: centroid AABB lo xyz, hi xyz (FP64)
