@@ -715,9 +715,27 @@ __device__ __forceinline__ bool beam_walk(const SceneView &s, bool want, const R
     // per-lane exact slab terms (the same arithmetic as packet_walk<ORIENTED>)
     const float sx = r.inv.x, sy = r.inv.y, sz = r.inv.z;
     const float kx = -r.oinv.x, ky = -r.oinv.y, kz = -r.oinv.z;
-    if (lane == 0) stk[0] = 0;
+    // The walk starts from the root's internal children, all pushed: their
+    // boxes lie in the root's, which holds every triangle, so testing them
+    // would only cull what the next step's tests of their children cull
+    // anyway (the beam test is monotonic under box inclusion), one step
+    // later.  A root with a leaf child (a scene of a few triangles) is
+    // walked from the root.
+    int sp;
+    {
+        const int rref = lane < 4 ? __float_as_int(__ldg(s.bnodes + 2 * lane).w) : kEmptyRef;
+        const unsigned rl = __ballot_sync(kFull, rref < 0 && rref != kEmptyRef);
+        const unsigned ri = __ballot_sync(kFull, rref >= 0);
+        if (rl) {
+            if (lane == 0) stk[0] = 0;
+            sp = 1;
+        } else {
+            sp = __popc(ri);
+            if (rref >= 0) stk[sp - 1 - __popc(ri & ((1u << lane) - 1u))] = rref;
+        }
+    }
     __syncwarp();
-    int sp = 1, steps = 0;
+    int steps = 0;
     while (true) {
         // up to kBeamNodes nodes, while their pushes (<= 4 each) fit the stack
         const int F = sp + 3 * kBeamNodes <= kBeamStack ? (sp < kBeamNodes ? sp : kBeamNodes) : 1;
