@@ -148,15 +148,26 @@ typedef struct {
  *             conservative test per child box for the whole packet, exact
  *             per-lane tests at the leaves) and the per-lane packet walk for
  *             the others; 1 = the per-lane packet walk for every packet.
- *             tile_w, blocks_per_sm, vpl_tile and walk change speed only,
- *             never the result (every pixel sums its VPLs in the same order
- *             and every segment gets the same answer from either walk). */
+ *  tile_order order in which the persistent grid takes the pixel tiles of a
+ *             single-view gather: 1 = scan order; 2 = most costly first, the
+ *             cost of each tile measured by a first pass over a sample of
+ *             the VPLs (64 per tile, every ceil(count / 64)-th in the gather's
+ *             VPL order), so that the slowest tiles do not start last and set
+ *             the end of the launch; 0 = cost order when the VPL set has at
+ *             least 8192 VPLs (the sample pass then costs under 1/128 of the
+ *             gather), else scan order.  Batched gathers and
+ *             vpl_gather_noalloc always take scan order.
+ *             tile_w, blocks_per_sm, vpl_tile, walk and tile_order change
+ *             speed only, never the result (every pixel sums its VPLs in the
+ *             same order and every segment gets the same answer from either
+ *             walk). */
 typedef struct {
     float d2_min, ray_eps;
     int32_t precision, visibility;
     int32_t tile_w, blocks_per_sm;
     int32_t vpl_tile;
     int32_t walk;
+    int32_t tile_order;
 } vpl_gather_params;
 
 /* caller-owned device buffers (see the layouts above) */

@@ -236,6 +236,7 @@ int check_gather(vpl_ctx *ctx, const vpl_gather_params *p, int gfmt, int vfmt)
     if (p->vpl_tile != 0 && p->vpl_tile != 16 && p->vpl_tile != 32 && p->vpl_tile != 64)
         return fail(ctx, VPL_ERR_INVALID_ARG, "vpl_tile must be 0, 16, 32 or 64");
     if (p->walk != 0 && p->walk != 1) return fail(ctx, VPL_ERR_INVALID_ARG, "walk must be 0 or 1");
+    if (p->tile_order < 0 || p->tile_order > 2) return fail(ctx, VPL_ERR_INVALID_ARG, "tile_order must be 0, 1 or 2");
     int want = p->precision == VPL_PREC_FP32 ? VPL_FORMAT_FP32 : VPL_FORMAT_FP16;
     if (gfmt != want || vfmt != want)
         return fail(ctx, VPL_ERR_INVALID_ARG, "buffer formats must be FP32 for precision 0 and FP16 otherwise");
@@ -312,6 +313,7 @@ GatherArgs gather_args(const vpl_gbuffer *g, const vpl_vpl_set *v, const vpl_gat
     a.blocks_per_sm = p->blocks_per_sm;
     a.vpl_tile = p->vpl_tile ? p->vpl_tile : 64;
     a.walk = p->walk;
+    a.tile_order = p->tile_order;
     a.g_pos = (const float4 *)g->pos;
     a.g_nrm = g->nrm;
     a.g_alb = g->albedo;
@@ -689,6 +691,7 @@ int vpl_gather_views(vpl_ctx *ctx, vpl_scene_id scene, int32_t n_views, const vp
     a.blocks_per_sm = params->blocks_per_sm;
     a.vpl_tile = params->vpl_tile ? params->vpl_tile : 64;
     a.walk = params->walk;
+    a.tile_order = params->tile_order;
     CK(ctx, gather_batch(ex, view_of(s), a, table.as<ViewDesc>(), n_views, (int)tiles,
                          tile_shift_of(params->tile_w), counter.as<int>(), n_vpls),
        "vpl_gather_views");
@@ -759,6 +762,7 @@ int vpl_gather_batch(vpl_ctx *ctx, vpl_scene_id scene, vpl_batch_id batch, const
     a.blocks_per_sm = params->blocks_per_sm;
     a.vpl_tile = params->vpl_tile ? params->vpl_tile : 64;
     a.walk = params->walk;
+    a.tile_order = params->tile_order;
     const vpl_ctx::Batch &b = it->second;
     CK(ctx, gather_batch(exec_of(ctx, stream), view_of(s), a, b.views, b.n_views, b.n_tiles, b.tile_shift, b.counter,
                          b.n_vpls),

@@ -104,6 +104,8 @@ struct GatherExtra {
     int64_t n_dbg;
     int8_t *dbg_vis;
     const uint32_t *v_order;          // VPLs in this order (per view from vpl_begin), else as given
+    const uint32_t *tile_order;       // tiles taken in this order, else in scan order
+    unsigned *tile_cost;              // when set: SM cycles each tile took (cost-sampling pass)
 };
 
 template <int VIS, int PREC, bool COUNT, bool DEBUG, bool BATCH>
@@ -125,6 +127,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
         if (lane == 0) tile = atomicAdd(e.tile_counter, 1);
         tile = __shfl_sync(kFull, tile, 0);
         if (tile >= e.n_tiles) break;
+        // cost order and the cost-sampling pass: single-view gathers only
+        constexpr bool kOrdered = !COUNT && !DEBUG && !BATCH;
+        if (kOrdered && e.tile_order) tile = (int)__ldg(e.tile_order + tile);
+        const long long clk0 = kOrdered && e.tile_cost ? clock64() : 0;
         // the view this tile belongs to
         int width = a.width, height = a.height, M = a.count, tiles_x = e.tiles_x, lt = tile;
         const float4 *g_pos = a.g_pos, *v_pos = a.v_pos;
@@ -195,8 +201,11 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                         vf.y *= vp.w;
                         vf.z *= vp.w;
                     }
+                    // a VPL without flux is staged with a zero normal: its
+                    // cosine is never positive, so no pixel wants it
+                    const bool lit = vf.x != 0.0f || vf.y != 0.0f || vf.z != 0.0f;
                     stage[wid][0][l] = vp;
-                    stage[wid][1][l] = load_attr(v_nrm, src, gfmt);
+                    stage[wid][1][l] = lit ? load_attr(v_nrm, src, gfmt) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     stage[wid][2][l] = vf;
                 }
             }
@@ -207,8 +216,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                 const float3 d = f3(xp) - y;
                 const float d2 = dot(d, d);
                 const float cosy = dot(ny, d), cosi = -dot(f3(xn), d);
-                const bool lit = xf.x != 0.0f || xf.y != 0.0f || xf.z != 0.0f;
-                const bool want = valid && lit && cosy > 0.0f && cosi > 0.0f && d2 > 0.0f;
+                const bool want = valid && cosy > 0.0f && cosi > 0.0f && d2 > 0.0f;
                 bool vis = true;
                 // most VPLs light none of a tile's pixels (a cosine or the
                 // flux is zero): the shadow rays are skipped warp-uniformly
@@ -250,6 +258,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                 }
             }
             __syncwarp();
+        }
+        if (kOrdered && e.tile_cost && lane == 0) {
+            const long long c = clock64() - clk0;
+            e.tile_cost[tile] = (unsigned)(c < 0 ? 0 : c > 0xffffffffLL ? 0xffffffffLL : c);
         }
         if (!DEBUG && inb && out) {
             float4 rho = valid ? load_attr(g_alb, p, gfmt) : make_float4(0, 0, 0, 0);
@@ -330,6 +342,8 @@ static GatherExtra single_view_extra(const GatherArgs &a, int *counter)
     e.n_dbg = 0;
     e.dbg_vis = nullptr;
     e.v_order = nullptr;
+    e.tile_order = nullptr;
+    e.tile_cost = nullptr;
     return e;
 }
 
@@ -386,19 +400,82 @@ static cudaError_t vpl_order(const Exec &ex, const SceneView &s, const float4 *v
     return radix_sort_pairs(ex, keys.as<uint64_t>(), order.as<uint32_t>(), nullptr, total, bits);
 }
 
+// ---------------------------------------------------------------------------
+// Tile order of a single-view gather.  The persistent grid takes tiles from a
+// queue; tiles differ in cost by an order of magnitude or more (a tile whose
+// pixels see most VPLs unblocked walks the BVH for nearly every VPL), and a
+// costly tile taken late sets the end of the launch.  With tile_order 2 (or
+// 0 and a large VPL set) a first pass gathers a sample of the VPLs into no
+// image and records the SM cycles each tile took; the main pass then takes
+// the tiles most costly first (ties in scan order).  The order changes speed
+// only: each pixel is summed by one thread over the same VPLs in the same
+// order either way.
+// ---------------------------------------------------------------------------
+constexpr int kCostSample = 64;         // sample VPLs per tile in the cost pass
+constexpr int kCostOrderAuto = 8192;    // tile_order 0: cost order from this many VPLs on
+
+__global__ void sample_order_kernel(const uint32_t *order, int64_t stride, int64_t n, uint32_t *sub)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sub[i] = order ? order[i * stride] : (uint32_t)(i * stride);
+}
+
+__global__ void cost_keys_kernel(const unsigned *cost, int n, uint64_t *keys, uint32_t *vals)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = 0xffffffffULL - cost[i]; // ascending keys: most costly first
+    vals[i] = (uint32_t)i;
+}
+
+static cudaError_t cost_order(const Exec &ex, const SceneView &s, const GatherArgs &a, const GatherExtra &e,
+                              int *counter, Tmp &tiles)
+{
+    const int64_t stride = (a.count + kCostSample - 1) / kCostSample;
+    const int64_t n_sample = (a.count + stride - 1) / stride;
+    Tmp sub, cost, keys;
+    VPL_TRY(sub.alloc(ex, sizeof(uint32_t) * n_sample));
+    VPL_TRY(cost.alloc(ex, sizeof(unsigned) * e.n_tiles));
+    VPL_TRY(keys.alloc(ex, sizeof(uint64_t) * e.n_tiles));
+    VPL_TRY(tiles.alloc(ex, sizeof(uint32_t) * e.n_tiles));
+    VPL_TRY(cudaMemsetAsync(cost.p, 0, sizeof(unsigned) * e.n_tiles, ex.stream));
+    sample_order_kernel<<<grid_for(n_sample, 256), 256, 0, ex.stream>>>(e.v_order, stride, n_sample,
+                                                                         sub.as<uint32_t>());
+    VPL_LAUNCHED(ex);
+    GatherArgs as = a;
+    as.count = (int32_t)n_sample;
+    as.out = nullptr; // the sample pass writes no image
+    GatherExtra es = e;
+    es.tile_counter = counter;
+    es.v_order = sub.as<uint32_t>();
+    es.tile_cost = cost.as<unsigned>();
+    VPL_TRY(cudaMemsetAsync(counter, 0, sizeof(int), ex.stream));
+    VPL_TRY((dispatch<false, false, false>(ex, s, as, es)));
+    cost_keys_kernel<<<grid_for(e.n_tiles, 256), 256, 0, ex.stream>>>(cost.as<unsigned>(), e.n_tiles,
+                                                                       keys.as<uint64_t>(), tiles.as<uint32_t>());
+    VPL_LAUNCHED(ex);
+    return radix_sort_pairs(ex, keys.as<uint64_t>(), tiles.as<uint32_t>(), nullptr, e.n_tiles, 32);
+}
+
 static cudaError_t run_gather(const Exec &ex, const SceneView &s, const GatherArgs &a, bool count,
                               unsigned long long *counters, const int32_t *pixels, int64_t n_pixels, int8_t *vis)
 {
     const int64_t npx = (int64_t)a.width * a.height;
     if (pixels == nullptr && npx == 0) return cudaSuccess;
     if (pixels != nullptr && n_pixels == 0) return cudaSuccess;
-    Tmp ctr, order;
-    VPL_TRY(ctr.alloc(ex, sizeof(int)));
+    Tmp ctr, order, tiles;
+    VPL_TRY(ctr.alloc(ex, 2 * sizeof(int)));
     VPL_TRY(cudaMemsetAsync(ctr.p, 0, sizeof(int), ex.stream));
     GatherExtra e = single_view_extra(a, ctr.as<int>());
     if (a.count > 1) {
         VPL_TRY(vpl_order(ex, s, a.v_pos, nullptr, 1, a.count, order));
         e.v_order = order.as<uint32_t>();
+    }
+    const bool by_cost = a.tile_order == 2 || (a.tile_order == 0 && a.count >= kCostOrderAuto);
+    if (!count && !pixels && by_cost && a.count > 0 && e.n_tiles > 1) {
+        VPL_TRY(cost_order(ex, s, a, e, ctr.as<int>() + 1, tiles));
+        e.tile_order = tiles.as<uint32_t>();
     }
     if (pixels) e.n_tiles = (int)((n_pixels + 31) / 32);
     e.counters = counters;

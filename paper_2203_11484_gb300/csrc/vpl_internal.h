@@ -123,6 +123,7 @@ struct GatherArgs {
     int32_t blocks_per_sm; // resident blocks per SM of the persistent grid (0 = occupancy limit)
     int32_t vpl_tile;      // VPLs staged per warp at a time: 16, 32 or 64
     int32_t walk;          // 0: beam walk for narrow shadow packets, 1: per-lane packet walk only
+    int32_t tile_order;    // 0 auto, 1 scan order, 2 costliest tiles first (single-view gathers)
     const float4 *g_pos;
     const void *g_nrm, *g_alb;
     const float4 *v_pos;

@@ -51,7 +51,7 @@ class vpl_gen_params(C.Structure):
 class vpl_gather_params(C.Structure):
     _fields_ = [("d2_min", C.c_float), ("ray_eps", C.c_float), ("precision", C.c_int32),
                 ("visibility", C.c_int32), ("tile_w", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("vpl_tile", C.c_int32), ("walk", C.c_int32)]
+                ("vpl_tile", C.c_int32), ("walk", C.c_int32), ("tile_order", C.c_int32)]
 
 
 class vpl_vpl_set(C.Structure):
@@ -210,6 +210,7 @@ def make_gather(p: W.GatherParams) -> vpl_gather_params:
     s.tile_w, s.blocks_per_sm = int(getattr(p, "tile_w", 0)), int(getattr(p, "blocks_per_sm", 0))
     s.vpl_tile = int(getattr(p, "vpl_tile", 0))
     s.walk = int(getattr(p, "walk", 0))
+    s.tile_order = int(getattr(p, "tile_order", 0))
     return s
 
 

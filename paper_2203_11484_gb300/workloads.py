@@ -84,6 +84,7 @@ class GatherParams:
     blocks_per_sm: int = 0    # persistent grid cap (0 = occupancy limit): speed only
     vpl_tile: int = 0         # VPLs staged per warp at a time (0 = 64): speed only
     walk: int = 0             # 0: beam walk for narrow shadow packets, 1: per-lane walk only: speed only
+    tile_order: int = 0       # 0 auto, 1 scan order, 2 costliest tiles first (sampled): speed only
 
 
 @dataclass

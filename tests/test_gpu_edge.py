@@ -192,6 +192,10 @@ def test_argument_errors(env):
     with pytest.raises(V.VplError):
         V.vpl_gather(ctx.h, sid, V.GBuffer.empty(8, 8), V.VplSet.empty(4),
                      W.GatherParams(1e-4, 1e-5, walk=2), torch.zeros((64, 4), device="cuda"))
+    for order in (-1, 3):             # tile orders are 0 (auto), 1 (scan) and 2 (cost)
+        with pytest.raises(V.VplError):
+            V.vpl_gather(ctx.h, sid, V.GBuffer.empty(8, 8), V.VplSet.empty(4),
+                         W.GatherParams(1e-4, 1e-5, tile_order=order), torch.zeros((64, 4), device="cuda"))
     for vt in (8, 48, 128, -16):      # VPL tiles are 16, 32 or 64 (0 = 64)
         with pytest.raises(V.VplError):
             V.vpl_gather(ctx.h, sid, V.GBuffer.empty(8, 8), V.VplSet.empty(4),

@@ -103,7 +103,8 @@ def test_large_precision_variants_on_crop(large):
 def test_large_beam_walk_equals_per_lane_walk(large):
     """The full 1920 x 1080 x 32768 launch on the 1M-triangle clutter with
     the beam walk (walk = 0) and with the per-lane packet walk only
-    (walk = 1): identical images."""
+    (walk = 1), the tiles taken most costly first (tile_order 0 picks that
+    order for 32768 VPLs) and in scan order: identical images."""
     import dataclasses
     V, ctx, wl, sid, _ = large
     view = wl.views[0]
@@ -113,10 +114,11 @@ def test_large_beam_walk_equals_per_lane_walk(large):
     V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
     V.vpl_generate(ctx.h, sid, cam, view.gen, vs)
     imgs = []
-    for walk in (0, 1):
+    for walk, order in ((0, 0), (1, 1), (0, 1)):
         out = torch.zeros((cam.width * cam.height, 4), dtype=torch.float32, device="cuda")
-        V.vpl_gather(ctx.h, sid, gb, vs, dataclasses.replace(view.gather, walk=walk), out)
+        V.vpl_gather(ctx.h, sid, gb, vs, dataclasses.replace(view.gather, walk=walk, tile_order=order), out)
         assert V.vpl_sync(ctx.h, check=False) == 0
         imgs.append(out)
     assert float(imgs[1].max()) > 0
     assert torch.equal(imgs[0], imgs[1])
+    assert torch.equal(imgs[2], imgs[1])

@@ -395,7 +395,8 @@ def test_beam_walk_equals_per_lane_walk_cornell(V, ctx, cornell):
 def test_beam_walk_equals_per_lane_walk(V, ctx, room, prec):
     """The full 1024 x 1024 x 4096 room launch with walk = 0 (beam walk for
     narrow packets) and walk = 1 (per-lane packet walk only): identical
-    images, and identical to the per-lane walk for every pixel tile shape."""
+    images, and identical to the per-lane walk for every pixel tile shape
+    and with the tiles taken most costly first (tile_order = 2)."""
     wl, sid, osc = room
     view = wl.views[0]
     cam = view.camera
@@ -405,13 +406,13 @@ def test_beam_walk_equals_per_lane_walk(V, ctx, room, prec):
     V.vpl_gbuffer_build(ctx.h, sid, cam, gb)
     V.vpl_generate(ctx.h, sid, cam, view.gen, vs)
     imgs = {}
-    for walk, tw in ((1, 8), (0, 8), (0, 4), (0, 32)):
+    for walk, tw, order in ((1, 8, 1), (0, 8, 0), (0, 4, 0), (0, 32, 0), (0, 8, 2), (0, 4, 2)):
         out = torch.zeros((cam.width * cam.height, 4), dtype=torch.float32, device="cuda")
-        params = dataclasses.replace(view.gather, precision=prec, walk=walk, tile_w=tw)
+        params = dataclasses.replace(view.gather, precision=prec, walk=walk, tile_w=tw, tile_order=order)
         V.vpl_gather(ctx.h, sid, gb, vs, params, out)
         assert V.vpl_sync(ctx.h, check=False) == 0
-        imgs[(walk, tw)] = out
-    ref = imgs[(1, 8)]
+        imgs[(walk, tw, order)] = out
+    ref = imgs[(1, 8, 1)]
     assert float(ref.max()) > 0
     for key, img in imgs.items():
         assert torch.equal(img, ref), key
