@@ -411,7 +411,10 @@ static cudaError_t vpl_order(const Exec &ex, const SceneView &s, const float4 *v
 // only: each pixel is summed by one thread over the same VPLs in the same
 // order either way.
 // ---------------------------------------------------------------------------
-constexpr int kCostSample = 64;         // sample VPLs per tile in the cost pass
+#ifndef VPL_COST_SAMPLE
+#define VPL_COST_SAMPLE 64
+#endif
+constexpr int kCostSample = VPL_COST_SAMPLE; // sample VPLs per tile in the cost pass (build-time knob)
 constexpr int kCostOrderAuto = 8192;    // tile_order 0: cost order from this many VPLs on
 
 __global__ void sample_order_kernel(const uint32_t *order, int64_t stride, int64_t n, uint32_t *sub)
