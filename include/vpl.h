@@ -274,7 +274,11 @@ VPL_API int vpl_light_vpls(vpl_ctx *ctx, vpl_scene_id scene, int32_t n, uint64_t
  * (rho/pi) * sum_i flux_i cos_i cos_y / (pi max(d^2, d2_min)) * V_i.
  * The sum runs over the VPLs in the Morton order of their positions (a
  * stable sort made on the stream for each call; it only changes FP32
- * rounding, and makes neighbouring shadow rays of a warp share BVH work). */
+ * rounding, and makes neighbouring shadow rays of a warp share BVH work).
+ * In cost order (params->tile_order) the call first gathers a sample of the
+ * VPLs into no image to time each pixel tile, then sorts the tiles.  Scratch
+ * (the VPL order; in cost order the tile costs and tile order, 16 B per tile)
+ * comes from the context's stream-ordered memory pool. */
 VPL_API int vpl_gather(vpl_ctx *ctx, vpl_scene_id scene, const vpl_gbuffer *gbuf,
                const vpl_vpl_set *vpls, const vpl_gather_params *params, float *out_rgba,
                vpl_stream stream);
