@@ -83,3 +83,25 @@ def test_binding_fails_loudly_without_library(tmp_path):
             vpl.load(str(tmp_path / "missing.so"))
     finally:
         vpl._L = saved
+
+
+def test_gather_params_marshal_every_field(tmp_path):
+    """make_gather copies every GatherParams field into the ctypes struct, and
+    each field of vpl_gather_params sits at the offset the C compiler gives it
+    (the speed-only knobs included: a slip would silently run the default)."""
+    from paper_2203_11484_gb300 import vpl, workloads as W
+    p = W.GatherParams(d2_min=0.25, ray_eps=0.5, precision=2, visibility=1, tile_w=16, blocks_per_sm=3,
+                       vpl_tile=32, walk=1, tile_order=2)
+    s = vpl.make_gather(p)
+    assert (s.d2_min, s.ray_eps) == (0.25, 0.5)
+    assert (s.precision, s.visibility, s.tile_w, s.blocks_per_sm, s.vpl_tile, s.walk, s.tile_order) == \
+        (2, 1, 16, 3, 32, 1, 2)
+    names = [f for f, _ in vpl.vpl_gather_params._fields_]
+    src = tmp_path / "off.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "vpl.h"\nint main(void){\n'
+                   + "".join(f'printf("%zu\\n", offsetof(vpl_gather_params, {n}));' for n in names)
+                   + "return 0;}\n")
+    exe = tmp_path / "off"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [getattr(vpl.vpl_gather_params, n).offset for n in names]
