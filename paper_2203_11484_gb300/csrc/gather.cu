@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
             __syncwarp();
             const int cnt = min(vt, M - base);
             for (int j = 0; j < cnt; j++) {
-                const float4 xp = stage[wid][0][j], xn = stage[wid][1][j], xf = stage[wid][2][j];
+                const float4 xp = stage[wid][0][j], xn = stage[wid][1][j];
                 const float3 d = f3(xp) - y;
                 const float d2 = dot(d, d);
                 const float cosy = dot(ny, d), cosi = -dot(f3(xn), d);
@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, VPL_GATHER_MIN_BLOCKS) gath
                     e.dbg_vis[((int64_t)tile * 32 + lane) * M + v] = want ? (vis ? 1 : 0) : -1;
                 }
                 if (want && vis) {
+                    const float4 xf = stage[wid][2][j]; // the flux only where the pair contributes
                     const float g = __fdividef(cosi * cosy, d2 * fmaxf(d2, d2min));
                     if (PREC == VPL_PREC_FP16_KAHAN) {
                         float yv = fmaf(xf.x, g, -cx), t = __fadd_rn(ax, yv);
